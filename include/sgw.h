@@ -1,0 +1,252 @@
+/*
+ * sgw.h -- C ABI of the GB300 (sm_103a) stochastic-GW hot path.
+ *
+ * The library computes the data-parallel core of stochastic GW in the sROI form:
+ * batched Chebyshev filtering and propagation of stochastic orbitals on a periodic
+ * real-space grid, the linear-response time-dependent-Hartree (TDH) step, the time
+ * ordering of the induced potential, the zeta propagation with the Sigma_c(t)
+ * accumulation, and the transform of Sigma to frequency and the QP solve.
+ *
+ * Conventions (all entry points):
+ *  - Grids are cubic, n^3 points with spacing h (bohr); n in {16, 32, 64, 128}.
+ *    A grid function is stored with x fastest: index g = (z*n + y)*n + x.
+ *  - A complex vector is interleaved complex64 ("c64": float re, float im), N_g
+ *    elements; a batch of B vectors is B contiguous vectors [B][N_g].
+ *  - The inner product is <a|b> = dV sum_g conj(a_g) b_g, dV = h^3.
+ *  - Hartree atomic units throughout.
+ *  - Pointers named *_dev are device pointers on the context's device; *_host are
+ *    host pointers.  The caller owns every input and output buffer; the library
+ *    owns only what the context allocates (plans, tables, projector data, scratch).
+ *  - Calls are asynchronous on the context's stream unless stated; those that
+ *    return host scalars synchronise that stream before returning.
+ *  - No call throws or aborts.  Errors are returned as an sgw_status; the message
+ *    of the last error is available from sgw_last_error().  A device-side failure
+ *    detected by a kernel (e.g. a bounded wait that ran out) is reported as
+ *    SGW_ETIMEOUT or SGW_ECUDA by the next synchronising call.
+ *  - Device buffers must be 16-byte aligned (cudaMalloc / torch allocations are).
+ */
+#ifndef SGW_H
+#define SGW_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sgw_ctx sgw_ctx;
+
+typedef enum {
+    SGW_OK = 0,
+    SGW_EINVAL = 1,    /* bad argument (size, pointer, unsupported grid) */
+    SGW_ENOMEM = 2,    /* device or host allocation failed */
+    SGW_ECUDA = 3,     /* a CUDA runtime call failed */
+    SGW_ESTATE = 4,    /* call out of order (e.g. no potential set yet) */
+    SGW_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    SGW_ENOCONV = 6    /* no root of the QP equation in the search window */
+} sgw_status;
+
+/* Library version string (static storage). */
+const char* sgw_version(void);
+
+/* Message of the last error on this context (static per context; NULL ctx gives the
+ * last error of sgw_setup_grid). */
+const char* sgw_last_error(const sgw_ctx* ctx);
+
+/*
+ * Create a context for an n^3 periodic grid of spacing h.
+ * Sec. 2.2: H is applied on a Fourier grid, FFT pairs switching between the position
+ * and momentum representations.  ecut > 0 enables the kinetic-energy cutoff of Sec. 2.2
+ * / Table 2 read as T(k) = min(|k|^2/2, ecut); ecut <= 0 disables it.
+ * max_batch: the largest number of vectors any later call will pass (sizes scratch:
+ * 3 * max_batch * N_g * 8 bytes).  stream: a cudaStream_t (NULL = default stream).
+ * device: CUDA device ordinal (made current for every call on this context).
+ */
+sgw_status sgw_setup_grid(sgw_ctx** out, int nx, int ny, int nz, double h, double ecut,
+                          int max_batch, int device, void* stream);
+
+/* Release the context and everything it allocated. */
+void sgw_destroy(sgw_ctx* ctx);
+
+/* Replace the stream used by later calls. */
+sgw_status sgw_set_stream(sgw_ctx* ctx, void* stream);
+
+/*
+ * Set H0 = T + V_loc + V_NL (Eq. 1 with the ionic pseudopotential split into a local
+ * part, folded with V_H[rho0] + V_xc into vloc, and Kleinman-Bylander projectors).
+ *  vloc_dev: [N_g] float, local potential (copied; the caller may free it afterwards).
+ *  KB part (Sec. 3: atomic operations where neighbouring atoms' spheres overlap):
+ *  n_atoms >= 0 atoms; atom a has nproj_host[a] in 1..4 projectors sharing the support
+ *  sup_idx_host[sup_off_host[a] .. sup_off_host[a+1]) (flat grid indices, each < N_g,
+ *  no repeats within an atom); beta_host holds, for each support point s of the whole
+ *  list, 4 floats beta_ap(r_s) (unused p padded), i.e. [total_support][4];
+ *  e_host is [n_atoms][4] projector energies E_ap.
+ *  V_NL psi = sum_{a,p} beta_ap E_ap dV sum_r beta_ap(r) psi(r).
+ * All host arrays are copied.  Passing n_atoms = 0 removes the nonlocal part.
+ */
+sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms,
+                             const int* nproj_host, const int64_t* sup_off_host,
+                             const int* sup_idx_host, const float* beta_host,
+                             const float* e_host);
+
+/* out_dev = H0 in_dev for a batch of B c64 vectors (test hook and the building block of
+ * every other call).  in and out may not alias. */
+sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batch);
+
+/*
+ * Spectral bounds by shifted power iteration (Sec. 2.1): n_iter power steps on H0 give
+ * E_max (Rayleigh quotient of the last iterate), n_iter steps on H0 - E_max give
+ * E_min - E_max.  The start vector is the Philox white noise of (seed, stream 0xB0B0,
+ * sample 0, vector 0).  The returned bounds are widened by margin * (E_max - E_min)
+ * on each side; raw_host (optional, 2 doubles) receives the unwidened estimates.
+ * The widened bounds are also stored in the context as the Chebyshev interval used by
+ * the filter and the propagators.  Synchronises.
+ */
+sgw_status sgw_spectral_bounds(sgw_ctx* ctx, int n_iter, uint64_t seed, double margin,
+                               double* emin_host, double* emax_host, double* raw_host);
+
+/* Set the Chebyshev interval [emin, emax] directly (H~ = (H - Ebar)/dE maps it to [-1,1]). */
+sgw_status sgw_set_spectrum(sgw_ctx* ctx, double emin, double emax);
+
+/*
+ * Coefficients a_0..a_{n_cheb} of the gapped Heaviside filter (Eq. 3), computed on the
+ * host in FP64: the least-squares fit of the step function at the 4 (n_cheb + 1)
+ * Chebyshev-Gauss nodes of [-1, 1], with zero weight for nodes inside
+ * [x(E_HOMO), x(E_LUMO)], plus ridge * M * |a|^2 (M the node count), solved through the
+ * normal equations: over all nodes the Gram matrix of T_0..T_N is diagonal (discrete
+ * orthogonality), so removing the gap nodes is a low-rank correction solved with the
+ * Woodbury identity and a Cholesky factorisation of the (gap nodes)^2 capacitance matrix.
+ * x(E) = (E - Ebar)/dE for the interval [emin, emax].
+ * coeffs_host: n_cheb + 1 doubles.  No context needed.
+ */
+sgw_status sgw_gapped_filter_coeffs(double e_homo, double e_lumo, double emin, double emax,
+                                    int n_cheb, double ridge, double* coeffs_host);
+
+/*
+ * Chebyshev propagator coefficients for e^{-i H dt} on [emin, emax] (host, FP64, no context):
+ * coeffs_host[2k], [2k+1] = re, im of (2 - delta_k0) (-i)^k J_k(dE |dt|), k = 0..cheb_deg
+ * (complex conjugated for dt < 0), and phase_host[0..1] = e^{-i Ebar dt}.  J_k by Miller's
+ * backward recurrence.  These are the coefficients sgw_propagate, sgw_tdh_response and
+ * sgw_sigma_c use.
+ */
+sgw_status sgw_propagator_coeffs(double emin, double emax, double dt, int cheb_deg, double* coeffs_host,
+                                 double* phase_host);
+
+/*
+ * Filtering (Eq. 3, Sec. 2.1): out = sum_{n=0}^{n_cheb} a_n T_n(H~) in, for a batch of c64
+ * vectors, by the Clenshaw recurrence in FP32 on the context's interval.  in and out may
+ * alias (in place).
+ */
+sgw_status sgw_filter_occupied(sgw_ctx* ctx, const double* coeffs_host, int n_cheb,
+                               const void* in_dev, void* out_dev, int batch);
+
+/*
+ * Philox4x32-10 white noise (Sec. 2.1 white-noise start orbitals): out[s][v] for
+ * s < n_samples, v < n_vec is the real Rademacher vector +-1/sqrt(dV) of
+ * (seed, stream_id, sample = sample0 + s, vector = v), stored as c64 with zero
+ * imaginary part.  Point g uses counter (g/4, v, sample, stream_id), key
+ * (seed mod 2^32, seed div 2^32), output word g mod 4, sign from its top bit.
+ */
+sgw_status sgw_white_noise(sgw_ctx* ctx, uint64_t seed, uint32_t stream_id, int sample0,
+                           int n_samples, int n_vec, void* out_dev);
+
+/*
+ * Split filtered white noise into the per-sample inputs of the two phases of Sec. 2.1.
+ * noise_dev, filt_dev: [n_samples][n_eta + 1] c64, the white noise and its filtered image
+ * (vector 0 of a sample is zeta-bar, vectors 1..n_eta the eta-bar_l).  Writes
+ *  eta_dev [n_samples][n_eta] c64: eta_l = P eta-bar_l;
+ *  zeta_dev [n_samples][2] c64: (zeta_occ = P zeta-bar, zeta_unocc = zeta-bar - P zeta-bar);
+ *  source_dev [n_samples][N_g] float: Re(zeta-bar) * phi, the source of the TDH kick.
+ * phi_dev: [N_g] float target orbital.
+ */
+sgw_status sgw_prepare_sample(sgw_ctx* ctx, const void* noise_dev, const void* filt_dev, const float* phi_dev,
+                              int n_samples, int n_eta, void* eta_dev, void* zeta_dev, float* source_dev);
+
+/*
+ * Plain propagation under H0: psi <- (e^{-i H0 dt})^{n_steps} psi for a batch of c64
+ * vectors (in place), each step the degree-cheb_deg Chebyshev expansion with Bessel
+ * coefficients (2 - delta_k0) (-i)^k J_k(dE |dt|) and phase e^{-i Ebar dt}; dt < 0
+ * propagates backwards.  dir_host (optional, [batch] int8: +1/-1) flips the direction
+ * of individual vectors (NULL: all +1).
+ */
+sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, double dt,
+                         int cheb_deg, const int8_t* dir_host);
+
+/*
+ * Linear-response TDH (Sec. 2.1, first phase) for n_samples Monte-Carlo samples.
+ *  eta_dev: [n_samples][n_eta] c64 filtered occupied stochastic orbitals (read only).
+ *  source_dev: [n_samples][N_g] float, the source zeta-bar * phi of each sample.
+ *  The perturbed copy of each eta is carried as its derivative with respect to the
+ *  kick strength (tangent-linear pair, the lambda -> 0 limit of the perturbed-minus-
+ *  unperturbed difference): d eta(0) = -i v_p eta(0), v_p = v_C * source.  Each step
+ *  holds H(t_j) = H0 + v_C * (rho(t_j) - rho(0)), rho = weight * sum_l |eta_l|^2 fixed
+ *  (weight <= 0 selects 2/n_eta).
+ *  uR_dev: [n_samples][n_steps + 1][N_g] float receives u^R(t_j) = v_C * d rho(t_j).
+ *  Requires 2 * n_samples * n_eta <= max_batch.
+ */
+sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* source_dev,
+                            int n_samples, int n_eta, int n_steps, double dt, int cheb_deg,
+                            double weight, float* uR_dev);
+
+/*
+ * Time ordering: u(t_j), j = 0..n_steps, from the causal u^R(t_j) of each grid point
+ * and sample: zero-pad to M (the smallest power of two >= 4 (n_steps + 1), M <= 4096),
+ * FFT with e^{+i omega t}, replace the negative-frequency half by its complex conjugate,
+ * inverse FFT.  uR_dev: [n_samples][n_steps+1][N_g] float; u_dev: same shape, c64.
+ */
+sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_samples,
+                          int n_steps);
+
+/*
+ * zeta propagation and Sigma(t) (Eq. 4, Eq. 5): for each sample, zeta_unocc propagates
+ * forward and zeta_occ backward under H0 for n_steps steps, and
+ *   Sigma(+t_j) =  dV sum_r phi(r) zeta_unocc(r, t_j) u(r, t_j),
+ *   Sigma(-t_j) = -dV sum_r phi(r) zeta_occ(r, -t_j) u(r, t_j),
+ * with the two one-sided limits averaged at t = 0.
+ *  zeta_dev: [n_samples][2] c64, (zeta_occ, zeta_unocc) per sample; propagated in place.
+ *  phi_dev: [N_g] float target orbital; u_dev: [n_samples][n_steps+1][N_g] c64.
+ *  sigma_dev: [n_samples][2 n_steps + 1] complex128 (index j + n_steps), written.
+ *  fp64_accum = 1 accumulates the reductions in FP64, 0 in FP32.
+ *  Requires 2 * n_samples <= max_batch.
+ */
+sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev,
+                       int n_samples, int n_steps, double dt, int cheb_deg, int fp64_accum,
+                       double* sigma_dev);
+
+/*
+ * sROI exchange (Eq. 6): x_dev[s] = -(1/n_eta) sum_l <phi eta_l | v_C | phi eta_l> in FP64,
+ * evaluated in k space.  eta_dev: [n_samples][n_eta] c64.  Requires n_eta <= max_batch.
+ */
+sgw_status sgw_exchange(sgw_ctx* ctx, const void* eta_dev, const float* phi_dev,
+                        int n_samples, int n_eta, double* x_dev);
+
+/*
+ * Sigma(omega) (Eq. 7, trapezoid over t_j, end weights 1/2):
+ *  out[w] = dt sum_j w_j Sigma(t_j) e^{-gamma^2 t_j^2/2} e^{i omega_w t_j}, j = -n_steps..n_steps,
+ * for the mean over n_samples rows of sigma_dev.  omega_dev: [n_omega] double;
+ * out_dev: [n_omega] complex128.  fp64 = 0 evaluates in FP32.
+ */
+sgw_status sgw_sigma_omega(sgw_ctx* ctx, const double* sigma_dev, int n_samples, int n_steps,
+                           double dt, double gamma, const double* omega_dev, int n_omega,
+                           int fp64, double* out_dev);
+
+/*
+ * QP equation (Eq. 6): the root of w = eps_ks + X + Re Sigma(w) - vxc nearest eps_ks for
+ * the sample means of Sigma(t) (sigma_dev [n_samples][2 n_steps + 1] complex128) and X
+ * (x_dev [n_samples] double): scan eps_ks +- window in steps of `step` for sign changes,
+ * take the bracket nearest eps_ks, bisect to 1e-10 Ha.  The standard error is
+ * Z * std_i(X_i + Re Sigma_i(eps_qp)) / sqrt(n_samples), Z = 1/(1 - dRe Sigma/dw).
+ * result_host: [4] doubles = (eps_qp, standard error, Re Sigma(eps_qp), Z).
+ * fp64 = 0 evaluates the transform in FP32.  Synchronises.  SGW_ENOCONV if no root.
+ */
+sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_dev,
+                         int n_samples, int n_steps, double dt, double gamma, double eps_ks,
+                         double vxc, double window, double step, int fp64,
+                         double* result_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGW_H */

@@ -1,0 +1,886 @@
+// C ABI of libsgw: context management, host orchestration of the kernels, and the FP64
+// host routines (gapped-filter coefficients, Bessel coefficients).  See include/sgw.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sgw.h"
+#include "sgw_internal.cuh"
+
+using cd = std::complex<double>;
+
+struct sgw_ctx {
+    int n = 0;
+    int64_t ng = 0;
+    double h = 0, dV = 0, L = 0, ecut = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int max_batch = 0;
+    double emin = 0, emax = 0;
+    bool have_spectrum = false;
+    bool have_potential = false;
+    // device memory owned by the context
+    float2* tw = nullptr;      // [n] exp(-2 pi i m / n)
+    float* vloc = nullptr;     // [ng]
+    float2* W = nullptr;       // [max_batch][ng]
+    float2* B1 = nullptr;      // [max_batch][ng]
+    float2* B2 = nullptr;      // [max_batch][ng]
+    sgw::VecInfo* info = nullptr;  // [max_batch]
+    float2* kbc = nullptr;     // [max_batch][n_proj]
+    sgw::KBDev kb;
+    double* scal = nullptr;    // small FP64 scratch
+    // lazily grown work areas
+    void* work[8] = {nullptr};
+    size_t work_sz[8] = {0};
+    float2* twM = nullptr;
+    int twM_n = 0;
+    std::vector<sgw::VecInfo> info_host;
+    std::string err;
+};
+
+static std::string g_setup_err;
+
+namespace {
+
+sgw_status fail(sgw_ctx* c, sgw_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_setup_err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess)                                                                        \
+            return fail(ctx, SGW_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+#define CKL()                                                                                         \
+    do {                                                                                              \
+        cudaError_t e_ = cudaGetLastError();                                                          \
+        if (e_ != cudaSuccess) return fail(ctx, SGW_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Grow work area `slot` to at least `bytes`.
+sgw_status work(sgw_ctx* ctx, int slot, size_t bytes, void** out) {
+    if (ctx->work_sz[slot] < bytes) {
+        if (ctx->work[slot]) {
+            cudaStreamSynchronize(ctx->stream);
+            cudaFree(ctx->work[slot]);
+            ctx->work[slot] = nullptr;
+            ctx->work_sz[slot] = 0;
+        }
+        cudaError_t e = cudaMalloc(&ctx->work[slot], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, SGW_ENOMEM, "work area allocation failed: " + std::to_string(bytes) + " bytes");
+        }
+        ctx->work_sz[slot] = bytes;
+    }
+    *out = ctx->work[slot];
+    return SGW_OK;
+}
+
+std::vector<float2> twiddles(int n) {
+    std::vector<float2> t(n);
+    for (int m = 0; m < n; ++m) {
+        const double a = -2.0 * M_PI * (double)m / (double)n;
+        t[m] = make_float2((float)std::cos(a), (float)std::sin(a));
+    }
+    return t;
+}
+
+float2 f2(cd z) { return make_float2((float)z.real(), (float)z.imag()); }
+
+// ---- Bessel J_k(a), k = 0..K, by Miller's backward recurrence normalised with
+//      J_0 + 2 sum_{k>=1} J_{2k} = 1 (J.C.P. Miller's method as given by
+//      Abramowitz & Stegun 9.12 / Numerical Recipes).
+std::vector<double> bessel_j(int K, double a) {
+    std::vector<double> J(K + 1, 0.0);
+    if (std::fabs(a) < 1e-300) {
+        J[0] = 1.0;
+        return J;
+    }
+    const int start = 2 * ((std::max(K, (int)std::ceil(std::fabs(a))) + 30 + (int)std::sqrt(40.0 * (K + 30))) / 2);
+    std::vector<double> j(start + 2, 0.0);
+    j[start + 1] = 0.0;
+    j[start] = 1e-30;
+    for (int k = start; k >= 1; --k) {
+        j[k - 1] = 2.0 * k / a * j[k] - j[k + 1];
+        if (std::fabs(j[k - 1]) > 1e250) {  // rescale to avoid overflow
+            for (int q = k - 1; q <= start + 1; ++q) j[q] *= 1e-250;
+        }
+    }
+    double norm = j[0];
+    for (int k = 2; k <= start; k += 2) norm += 2.0 * j[k];
+    for (int k = 0; k <= K; ++k) J[k] = j[k] / norm;
+    return J;
+}
+
+// Clenshaw step plan of a Chebyshev sum sum_{k=0}^{K} c_k T_k(H~) psi (optionally times a phase).
+struct Step {
+    cd cpsi[2], ch[2], c2[2];
+    int b1;     // 0: psi, 1: X, 2: Y
+    int b2;     // -1: none, 1: X, 2: Y
+    int out;    // 1: X, 2: Y, 3: final output
+};
+
+// c[set][k]: coefficient sets (set 1 only used when two_sets).  ch multiplies 2 H~ b1.
+std::vector<Step> clenshaw_plan(const std::vector<cd>* c, const cd* phase, int K) {
+    std::vector<Step> plan;
+    if (K == 0) return plan;
+    if (K == 1) {  // S = c0 psi + c1 H~ psi
+        Step s;
+        for (int q = 0; q < 2; ++q) {
+            s.cpsi[q] = phase[q] * c[q][0];
+            s.ch[q] = phase[q] * c[q][1] * 0.5;
+            s.c2[q] = 0;
+        }
+        s.b1 = 0; s.b2 = -1; s.out = 3;
+        plan.push_back(s);
+        return plan;
+    }
+    // first: b_{K-1} = c_{K-1} psi + 2 c_K H~ psi  -> X
+    {
+        Step s;
+        for (int q = 0; q < 2; ++q) { s.cpsi[q] = c[q][K - 1]; s.ch[q] = c[q][K]; s.c2[q] = 0; }
+        s.b1 = 0; s.b2 = -1; s.out = 1;
+        plan.push_back(s);
+    }
+    if (K == 2) {  // S = (c0 - c2) psi + H~ b1
+        Step s;
+        for (int q = 0; q < 2; ++q) { s.cpsi[q] = phase[q] * (c[q][0] - c[q][2]); s.ch[q] = phase[q] * 0.5; s.c2[q] = 0; }
+        s.b1 = 1; s.b2 = -1; s.out = 3;
+        plan.push_back(s);
+        return plan;
+    }
+    // second: b_{K-2} = (c_{K-2} - c_K) psi + 2 H~ b_{K-1}  -> Y
+    {
+        Step s;
+        for (int q = 0; q < 2; ++q) { s.cpsi[q] = c[q][K - 2] - c[q][K]; s.ch[q] = 1.0; s.c2[q] = 0; }
+        s.b1 = 1; s.b2 = -1; s.out = 2;
+        plan.push_back(s);
+    }
+    // b_{k+1} lives in `last`, b_{k+2} in `prev`; b_k overwrites b_{k+2}
+    int last = 2, prev = 1;
+    for (int k = K - 3; k >= 1; --k) {
+        Step s;
+        for (int q = 0; q < 2; ++q) { s.cpsi[q] = c[q][k]; s.ch[q] = 1.0; s.c2[q] = -1.0; }
+        s.b1 = last; s.b2 = prev; s.out = prev;
+        plan.push_back(s);
+        std::swap(last, prev);
+    }
+    Step s;
+    for (int q = 0; q < 2; ++q) { s.cpsi[q] = phase[q] * c[q][0]; s.ch[q] = phase[q] * 0.5; s.c2[q] = -phase[q]; }
+    s.b1 = last; s.b2 = prev; s.out = 3;
+    plan.push_back(s);
+    return plan;
+}
+
+// Run one Chebyshev sum over a batch.  psi_in: real-space input; out: result (may alias psi_in).
+// W must hold the forward xy transform of psi_in on entry when w_ready; on exit it holds the
+// transform of the output when want_wout.
+sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2* psi_in, float2* out, int batch,
+                      const float* vpot, const float* dvpot, const sgw::VecInfo* info, bool w_ready, bool want_wout) {
+    cudaStream_t st = ctx->stream;
+    const int n = ctx->n;
+    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
+    const double ebar = 0.5 * (ctx->emax + ctx->emin), de = 0.5 * (ctx->emax - ctx->emin);
+    if (plan.empty()) {
+        if (out != psi_in) CK(cudaMemcpyAsync(out, psi_in, sizeof(float2) * ctx->ng * batch, cudaMemcpyDeviceToDevice, st));
+        return SGW_OK;
+    }
+    if (!w_ready) {
+        sgw::launch_plane_fwd(n, psi_in, ctx->W, batch, ctx->tw, st);
+        CKL();
+    }
+    auto buf = [&](int id) -> float2* {
+        return id == 0 ? const_cast<float2*>(psi_in) : (id == 1 ? ctx->B1 : (id == 2 ? ctx->B2 : out));
+    };
+    for (size_t i = 0; i < plan.size(); ++i) {
+        const Step& s = plan[i];
+        const float2* b1 = buf(s.b1);
+        if (ctx->kb.n_atoms > 0) {
+            sgw::launch_kb_project(n, ctx->kb, b1, batch, (float)ctx->dV, ctx->kbc, st);
+            CKL();
+        }
+        sgw::launch_pencil(n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, st);
+        CKL();
+        sgw::StepArgs a{};
+        a.W = ctx->W;
+        const bool last = (i + 1 == plan.size());
+        a.Wout = (!last || want_wout) ? ctx->W : nullptr;
+        a.b1 = b1;
+        a.b2 = s.b2 >= 0 ? buf(s.b2) : nullptr;
+        a.psi = psi_in;
+        a.out = buf(s.out);
+        a.vpot = vpot;
+        a.dvpot = dvpot;
+        a.info = info;
+        a.kbc = ctx->kb.n_atoms > 0 ? ctx->kbc : nullptr;
+        a.pt_ptr = ctx->kb.pt_ptr;
+        a.pt_atom = ctx->kb.pt_atom;
+        a.pt_beta = ctx->kb.pt_beta;
+        a.n_proj = ctx->kb.n_proj;
+        a.ebar = (float)ebar;
+        a.alpha = (float)(2.0 / de);
+        for (int q = 0; q < 2; ++q) {
+            a.coef.cpsi[q] = f2(s.cpsi[q]);
+            a.coef.ch[q] = f2(s.ch[q]);
+            a.coef.c2[q] = f2(s.c2[q]);
+        }
+        sgw::launch_plane_step(n, a, batch, ctx->tw, st);
+        CKL();
+    }
+    return SGW_OK;
+}
+
+// Per-vector descriptors live in device memory; re-upload only when they change.  The host copy
+// kept in the context is the source of the (stream-ordered) copy.
+sgw_status upload_info(sgw_ctx* ctx, const std::vector<sgw::VecInfo>& v) {
+    if (v.size() <= ctx->info_host.size() &&
+        std::memcmp(v.data(), ctx->info_host.data(), sizeof(sgw::VecInfo) * v.size()) == 0)
+        return SGW_OK;
+    ctx->info_host = v;
+    CK(cudaMemcpyAsync(ctx->info, ctx->info_host.data(), sizeof(sgw::VecInfo) * v.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return SGW_OK;
+}
+
+void prop_coeffs(sgw_ctx* ctx, double dt, int K, std::vector<cd> c[2], cd phase[2]) {
+    const double ebar = 0.5 * (ctx->emax + ctx->emin), de = 0.5 * (ctx->emax - ctx->emin);
+    const std::vector<double> J = bessel_j(K, de * std::fabs(dt));
+    c[0].resize(K + 1);
+    c[1].resize(K + 1);
+    cd mi(1.0, 0.0);
+    for (int k = 0; k <= K; ++k) {
+        const cd v = (k == 0 ? 1.0 : 2.0) * J[k] * mi;      // (2 - delta_k0) (-i)^k J_k
+        c[0][k] = dt >= 0 ? v : std::conj(v);
+        c[1][k] = std::conj(c[0][k]);
+        mi *= cd(0.0, -1.0);
+    }
+    phase[0] = std::exp(cd(0.0, -ebar * dt));
+    phase[1] = std::conj(phase[0]);
+}
+
+sgw_status check_ctx(sgw_ctx* ctx, bool need_pot) {
+    if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return fail(ctx, SGW_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    if (need_pot && !ctx->have_potential) return fail(ctx, SGW_ESTATE, "sgw_set_potential has not been called");
+    return SGW_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* sgw_version(void) { return "sgw-gb300 0.1 (sm_103a)"; }
+
+const char* sgw_last_error(const sgw_ctx* ctx) { return ctx ? ctx->err.c_str() : g_setup_err.c_str(); }
+
+sgw_status sgw_setup_grid(sgw_ctx** out, int nx, int ny, int nz, double h, double ecut, int max_batch, int device,
+                          void* stream) {
+    sgw_ctx* ctx = nullptr;
+    if (!out) return fail(nullptr, SGW_EINVAL, "out is null");
+    *out = nullptr;
+    if (nx != ny || ny != nz || !sgw::grid_supported(nx))
+        return fail(nullptr, SGW_EINVAL, "grid must be cubic with n in {16,32,64,128}");
+    if (!(h > 0) || max_batch < 1) return fail(nullptr, SGW_EINVAL, "h must be > 0 and max_batch >= 1");
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, SGW_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
+    ctx = new (std::nothrow) sgw_ctx();
+    if (!ctx) return fail(nullptr, SGW_ENOMEM, "host allocation failed");
+    ctx->n = nx;
+    ctx->ng = (int64_t)nx * nx * nx;
+    ctx->h = h;
+    ctx->dV = h * h * h;
+    ctx->L = nx * h;
+    ctx->ecut = ecut > 0 ? ecut : 0.0;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->max_batch = max_batch;
+    const size_t vb = sizeof(float2) * ctx->ng * (size_t)max_batch;
+    auto tw = twiddles(nx);
+    bool ok = cudaMalloc(&ctx->tw, sizeof(float2) * nx) == cudaSuccess &&
+              cudaMalloc(&ctx->vloc, sizeof(float) * ctx->ng) == cudaSuccess &&
+              cudaMalloc(&ctx->W, vb) == cudaSuccess && cudaMalloc(&ctx->B1, vb) == cudaSuccess &&
+              cudaMalloc(&ctx->B2, vb) == cudaSuccess &&
+              cudaMalloc(&ctx->info, sizeof(sgw::VecInfo) * max_batch) == cudaSuccess &&
+              cudaMalloc(&ctx->scal, 64 * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        std::string m = "device allocation failed for " + std::to_string(3.0 * vb / 1e9) + " GB of scratch";
+        sgw_destroy(ctx);
+        return fail(nullptr, SGW_ENOMEM, m);
+    }
+    e = cudaMemcpy(ctx->tw, tw.data(), sizeof(float2) * nx, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = sgw::grid_init_attributes(nx);
+    if (e == cudaSuccess) e = cudaMemset(ctx->vloc, 0, sizeof(float) * ctx->ng);
+    if (e != cudaSuccess) {
+        std::string m = std::string("setup: ") + cudaGetErrorString(e);
+        sgw_destroy(ctx);
+        return fail(nullptr, SGW_ECUDA, m);
+    }
+    *out = ctx;
+    return SGW_OK;
+}
+
+void sgw_destroy(sgw_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    void* ptrs[] = {ctx->tw, ctx->vloc, ctx->W, ctx->B1, ctx->B2, ctx->info, ctx->kbc, ctx->scal, ctx->twM,
+                    ctx->kb.atom_nproj, ctx->kb.atom_off, ctx->kb.sup_idx, ctx->kb.sup_beta, ctx->kb.atom_e,
+                    ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 8; ++i)
+        if (ctx->work[i]) cudaFree(ctx->work[i]);
+    delete ctx;
+}
+
+sgw_status sgw_set_stream(sgw_ctx* ctx, void* stream) {
+    if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    ctx->stream = (cudaStream_t)stream;
+    return SGW_OK;
+}
+
+sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, const int* nproj_host,
+                             const int64_t* sup_off_host, const int* sup_idx_host, const float* beta_host,
+                             const float* e_host) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (!vloc_dev) return fail(ctx, SGW_EINVAL, "vloc_dev is null");
+    if (n_atoms < 0) return fail(ctx, SGW_EINVAL, "n_atoms < 0");
+    CK(cudaMemcpyAsync(ctx->vloc, vloc_dev, sizeof(float) * ctx->ng, cudaMemcpyDeviceToDevice, ctx->stream));
+    // drop any previous KB data
+    CK(cudaStreamSynchronize(ctx->stream));
+    void* old[] = {ctx->kb.atom_nproj, ctx->kb.atom_off, ctx->kb.sup_idx, ctx->kb.sup_beta, ctx->kb.atom_e,
+                   ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta, ctx->kbc};
+    for (void* p : old)
+        if (p) cudaFree(p);
+    ctx->kb = sgw::KBDev();
+    ctx->kbc = nullptr;
+    if (n_atoms > 0) {
+        if (!nproj_host || !sup_off_host || !sup_idx_host || !beta_host || !e_host)
+            return fail(ctx, SGW_EINVAL, "KB arrays must be non-null when n_atoms > 0");
+        if (sup_off_host[0] != 0) return fail(ctx, SGW_EINVAL, "sup_off[0] must be 0");
+        for (int a = 0; a < n_atoms; ++a) {
+            if (nproj_host[a] < 1 || nproj_host[a] > 4) return fail(ctx, SGW_EINVAL, "nproj must be in 1..4");
+            if (sup_off_host[a + 1] < sup_off_host[a]) return fail(ctx, SGW_EINVAL, "sup_off must be non-decreasing");
+        }
+        const int64_t nsup = sup_off_host[n_atoms];
+        if (nsup > INT32_MAX) return fail(ctx, SGW_EINVAL, "too many support points");
+        for (int64_t i = 0; i < nsup; ++i)
+            if (sup_idx_host[i] < 0 || sup_idx_host[i] >= ctx->ng) return fail(ctx, SGW_EINVAL, "support index out of range");
+        // point-major CSR (counting sort by grid index)
+        std::vector<int> cnt(ctx->ng + 1, 0);
+        for (int64_t i = 0; i < nsup; ++i) cnt[sup_idx_host[i] + 1]++;
+        for (int64_t g = 0; g < ctx->ng; ++g) cnt[g + 1] += cnt[g];
+        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
+        std::vector<int> pt_atom(nsup);
+        std::vector<float4> pt_beta(nsup), sup_beta(nsup), atom_e(n_atoms);
+        for (int a = 0; a < n_atoms; ++a) {
+            atom_e[a] = make_float4(e_host[4 * a], e_host[4 * a + 1], e_host[4 * a + 2], e_host[4 * a + 3]);
+            for (int64_t i = sup_off_host[a]; i < sup_off_host[a + 1]; ++i) {
+                float4 b = make_float4(beta_host[4 * i], beta_host[4 * i + 1], beta_host[4 * i + 2], beta_host[4 * i + 3]);
+                if (nproj_host[a] < 4) b.w = 0.f;
+                if (nproj_host[a] < 3) b.z = 0.f;
+                if (nproj_host[a] < 2) b.y = 0.f;
+                sup_beta[i] = b;
+                const int p = pos[sup_idx_host[i]]++;
+                pt_atom[p] = a;
+                pt_beta[p] = b;
+            }
+        }
+        sgw::KBDev& kb = ctx->kb;
+        kb.n_atoms = n_atoms;
+        kb.n_proj = 4 * n_atoms;
+        kb.n_sup = nsup;
+        bool ok = cudaMalloc(&kb.atom_nproj, sizeof(int) * n_atoms) == cudaSuccess &&
+                  cudaMalloc(&kb.atom_off, sizeof(int64_t) * (n_atoms + 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.sup_idx, sizeof(int) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.sup_beta, sizeof(float4) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.atom_e, sizeof(float4) * n_atoms) == cudaSuccess &&
+                  cudaMalloc(&kb.pt_ptr, sizeof(int) * (ctx->ng + 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.pt_atom, sizeof(int) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.pt_beta, sizeof(float4) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
+                  cudaMalloc(&ctx->kbc, sizeof(float2) * (size_t)kb.n_proj * ctx->max_batch) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(ctx, SGW_ENOMEM, "KB device allocation failed");
+        }
+        CK(cudaMemcpy(kb.atom_nproj, nproj_host, sizeof(int) * n_atoms, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.atom_off, sup_off_host, sizeof(int64_t) * (n_atoms + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.sup_idx, sup_idx_host, sizeof(int) * nsup, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.sup_beta, sup_beta.data(), sizeof(float4) * nsup, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.atom_e, atom_e.data(), sizeof(float4) * n_atoms, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.pt_ptr, cnt.data(), sizeof(int) * (ctx->ng + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.pt_atom, pt_atom.data(), sizeof(int) * nsup, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.pt_beta, pt_beta.data(), sizeof(float4) * nsup, cudaMemcpyHostToDevice));
+    }
+    ctx->have_potential = true;
+    return SGW_OK;
+}
+
+sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batch) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (batch < 0 || batch > ctx->max_batch) return fail(ctx, SGW_EINVAL, "batch out of range");
+    if (batch == 0) return SGW_OK;
+    if (!in_dev || !out_dev || in_dev == out_dev) return fail(ctx, SGW_EINVAL, "bad in/out pointers");
+    std::vector<sgw::VecInfo> info(batch, sgw::VecInfo{0, -1, -1, 0});
+    if ((s = upload_info(ctx, info))) return s;
+    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
+    const float2* in = (const float2*)in_dev;
+    sgw::launch_plane_fwd(ctx->n, in, ctx->W, batch, ctx->tw, ctx->stream);
+    CKL();
+    if (ctx->kb.n_atoms > 0) {
+        sgw::launch_kb_project(ctx->n, ctx->kb, in, batch, (float)ctx->dV, ctx->kbc, ctx->stream);
+        CKL();
+    }
+    sgw::launch_pencil(ctx->n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, ctx->stream);
+    CKL();
+    sgw::StepArgs a{};
+    a.W = ctx->W;
+    a.Wout = nullptr;
+    a.b1 = in;
+    a.out = (float2*)out_dev;
+    a.vpot = ctx->vloc;
+    a.info = ctx->info;
+    a.kbc = ctx->kb.n_atoms > 0 ? ctx->kbc : nullptr;
+    a.pt_ptr = ctx->kb.pt_ptr;
+    a.pt_atom = ctx->kb.pt_atom;
+    a.pt_beta = ctx->kb.pt_beta;
+    a.n_proj = ctx->kb.n_proj;
+    a.ebar = 0.f;
+    a.alpha = 1.f;
+    for (int q = 0; q < 2; ++q) {
+        a.coef.cpsi[q] = make_float2(0.f, 0.f);
+        a.coef.ch[q] = make_float2(1.f, 0.f);
+        a.coef.c2[q] = make_float2(0.f, 0.f);
+    }
+    sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_set_spectrum(sgw_ctx* ctx, double emin, double emax) {
+    if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    if (!(emax > emin)) return fail(ctx, SGW_EINVAL, "emax must exceed emin");
+    ctx->emin = emin;
+    ctx->emax = emax;
+    ctx->have_spectrum = true;
+    return SGW_OK;
+}
+
+sgw_status sgw_spectral_bounds(sgw_ctx* ctx, int n_iter, uint64_t seed, double margin, double* emin_host,
+                               double* emax_host, double* raw_host) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (n_iter < 1 || !emin_host || !emax_host || !(margin >= 0))
+        return fail(ctx, SGW_EINVAL, "bad spectral-bounds arguments");
+    cudaStream_t st = ctx->stream;
+    float2 *v, *w;
+    void* p;
+    if ((s = work(ctx, 0, sizeof(float2) * ctx->ng * 2, &p))) return s;
+    v = (float2*)p;
+    w = v + ctx->ng;
+    double* est = ctx->scal + 8;   // est[0] E_max estimate, est[1] shifted estimate
+    sgw::launch_noise((int)ctx->ng, seed, 0xB0B0u, 0, 1, 1, (float)(1.0 / std::sqrt(ctx->dV)), v, st);
+    CKL();
+    for (int pass = 0; pass < 2; ++pass) {
+        if (pass == 1) {
+            sgw::launch_noise((int)ctx->ng, seed, 0xB0B0u, 0, 1, 1, (float)(1.0 / std::sqrt(ctx->dV)), v, st);
+            CKL();
+        }
+        for (int it = 0; it < n_iter; ++it) {
+            if ((s = sgw_apply_h(ctx, v, w, 1))) return s;
+            sgw::launch_dot2((int)ctx->ng, v, w, ctx->scal, st);
+            CKL();
+            sgw::launch_power_update((int)ctx->ng, w, v, ctx->scal, est + pass, pass == 1 ? est : nullptr,
+                                     (float)ctx->dV, st);
+            CKL();
+        }
+    }
+    double e[2];
+    CK(cudaMemcpyAsync(e, est, sizeof(e), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double emax = e[0], emin = e[0] + e[1];
+    if (raw_host) {
+        raw_host[0] = emin;
+        raw_host[1] = emax;
+    }
+    const double wd = emax - emin;
+    *emin_host = emin - margin * wd;
+    *emax_host = emax + margin * wd;
+    return sgw_set_spectrum(ctx, *emin_host, *emax_host);
+}
+
+sgw_status sgw_gapped_filter_coeffs(double e_homo, double e_lumo, double emin, double emax, int n_cheb, double ridge,
+                                    double* coeffs_host) {
+    sgw_ctx* ctx = nullptr;
+    if (!coeffs_host || n_cheb < 0 || !(emax > emin) || !(e_lumo >= e_homo) || !(ridge > 0))
+        return fail(ctx, SGW_EINVAL, "bad gapped-filter arguments");
+    const double ebar = 0.5 * (emax + emin), de = 0.5 * (emax - emin);
+    const double xh = (e_homo - ebar) / de, xl = (e_lumo - ebar) / de;
+    const int N1 = n_cheb + 1;
+    const int M = 4 * N1;
+    // Over all M Chebyshev-Gauss nodes sum_m T_j T_k = D_jj delta_jk (D_00 = M, D_jj = M/2): the normal
+    // matrix of the fit without the gap nodes is D + rho - U^T U, U the rows of the gap nodes.  Solve it
+    // through the Woodbury identity with the small capacitance matrix I - U D'^-1 U^T (Cholesky).
+    std::vector<double> dinv(N1), rhs(N1, 0.0), Tk(N1);
+    const double rho = ridge * M;
+    for (int k = 0; k < N1; ++k) dinv[k] = 1.0 / ((k == 0 ? (double)M : 0.5 * M) + rho);
+    std::vector<std::vector<double>> U;
+    for (int m = 0; m < M; ++m) {
+        const double th = M_PI * (m + 0.5) / M;
+        const double x = std::cos(th);
+        const bool keep = (x <= xh) || (x >= xl);
+        for (int k = 0; k < N1; ++k) Tk[k] = std::cos(k * th);
+        if (keep) {
+            if (x <= xh)
+                for (int k = 0; k < N1; ++k) rhs[k] += Tk[k];
+        } else {
+            U.push_back(Tk);
+        }
+    }
+    const int G = (int)U.size();
+    // y = D'^-1 rhs
+    std::vector<double> y(N1);
+    for (int k = 0; k < N1; ++k) y[k] = dinv[k] * rhs[k];
+    if (G > 0) {
+        // C = I - U D'^-1 U^T ; solve C z = U y ; a = y + D'^-1 U^T z
+        std::vector<double> C((size_t)G * G), z(G);
+        for (int i = 0; i < G; ++i) {
+            for (int j = 0; j <= i; ++j) {
+                double acc = 0;
+                for (int k = 0; k < N1; ++k) acc += U[i][k] * dinv[k] * U[j][k];
+                C[(size_t)i * G + j] = C[(size_t)j * G + i] = (i == j ? 1.0 : 0.0) - acc;
+            }
+            double acc = 0;
+            for (int k = 0; k < N1; ++k) acc += U[i][k] * y[k];
+            z[i] = acc;
+        }
+        // Cholesky C = L L^T (C is positive definite because the regularised normal matrix is)
+        for (int j = 0; j < G; ++j) {
+            double d = C[(size_t)j * G + j];
+            for (int k = 0; k < j; ++k) d -= C[(size_t)j * G + k] * C[(size_t)j * G + k];
+            if (!(d > 0)) return fail(ctx, SGW_ENOCONV, "gapped-filter capacitance matrix is not positive definite");
+            d = std::sqrt(d);
+            C[(size_t)j * G + j] = d;
+            for (int i = j + 1; i < G; ++i) {
+                double t = C[(size_t)i * G + j];
+                for (int k = 0; k < j; ++k) t -= C[(size_t)i * G + k] * C[(size_t)j * G + k];
+                C[(size_t)i * G + j] = t / d;
+            }
+        }
+        for (int i = 0; i < G; ++i) {  // forward
+            double t = z[i];
+            for (int k = 0; k < i; ++k) t -= C[(size_t)i * G + k] * z[k];
+            z[i] = t / C[(size_t)i * G + i];
+        }
+        for (int i = G - 1; i >= 0; --i) {  // backward
+            double t = z[i];
+            for (int k = i + 1; k < G; ++k) t -= C[(size_t)k * G + i] * z[k];
+            z[i] = t / C[(size_t)i * G + i];
+        }
+        for (int k = 0; k < N1; ++k) {
+            double acc = 0;
+            for (int i = 0; i < G; ++i) acc += U[i][k] * z[i];
+            y[k] += dinv[k] * acc;
+        }
+    }
+    for (int k = 0; k < N1; ++k) coeffs_host[k] = y[k];
+    return SGW_OK;
+}
+
+sgw_status sgw_propagator_coeffs(double emin, double emax, double dt, int cheb_deg, double* coeffs_host,
+                                 double* phase_host) {
+    if (!coeffs_host || !phase_host || cheb_deg < 0 || !(emax > emin))
+        return fail(nullptr, SGW_EINVAL, "bad propagator-coefficient arguments");
+    sgw_ctx tmp;
+    tmp.emin = emin;
+    tmp.emax = emax;
+    std::vector<cd> c[2];
+    cd ph[2];
+    prop_coeffs(&tmp, dt, cheb_deg, c, ph);
+    for (int k = 0; k <= cheb_deg; ++k) {
+        coeffs_host[2 * k] = c[0][k].real();
+        coeffs_host[2 * k + 1] = c[0][k].imag();
+    }
+    phase_host[0] = ph[0].real();
+    phase_host[1] = ph[0].imag();
+    return SGW_OK;
+}
+
+sgw_status sgw_filter_occupied(sgw_ctx* ctx, const double* coeffs_host, int n_cheb, const void* in_dev, void* out_dev,
+                               int batch) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
+    if (!coeffs_host || n_cheb < 0 || batch < 0 || batch > ctx->max_batch || !in_dev || !out_dev)
+        return fail(ctx, SGW_EINVAL, "bad filter arguments");
+    if (batch == 0) return SGW_OK;
+    std::vector<cd> c[2];
+    c[0].assign(coeffs_host, coeffs_host + n_cheb + 1);
+    c[1] = c[0];
+    const cd one[2] = {1.0, 1.0};
+    if (n_cheb == 0) {
+        // out = a_0 in : run an empty plan then scale on the host side would need a kernel; use K=1 with c1=0
+        c[0].push_back(0.0);
+        c[1].push_back(0.0);
+        n_cheb = 1;
+    }
+    const std::vector<Step> plan = clenshaw_plan(c, one, n_cheb);
+    std::vector<sgw::VecInfo> info(batch, sgw::VecInfo{0, -1, -1, 0});
+    if ((s = upload_info(ctx, info))) return s;
+    return run_series(ctx, plan, (const float2*)in_dev, (float2*)out_dev, batch, ctx->vloc, nullptr, ctx->info, false,
+                      false);
+}
+
+sgw_status sgw_white_noise(sgw_ctx* ctx, uint64_t seed, uint32_t stream_id, int sample0, int n_samples, int n_vec,
+                           void* out_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 0 || n_vec < 0 || sample0 < 0 || (!out_dev && n_samples * n_vec > 0))
+        return fail(ctx, SGW_EINVAL, "bad noise arguments");
+    sgw::launch_noise((int)ctx->ng, seed, stream_id, sample0, n_samples, n_vec, (float)(1.0 / std::sqrt(ctx->dV)),
+                      (float2*)out_dev, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_prepare_sample(sgw_ctx* ctx, const void* noise_dev, const void* filt_dev, const float* phi_dev,
+                              int n_samples, int n_eta, void* eta_dev, void* zeta_dev, float* source_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 0 || n_eta < 1) return fail(ctx, SGW_EINVAL, "bad prepare arguments");
+    if (n_samples == 0) return SGW_OK;
+    if (!noise_dev || !filt_dev || !phi_dev || !eta_dev || !zeta_dev || !source_dev)
+        return fail(ctx, SGW_EINVAL, "null prepare pointers");
+    sgw::launch_prepare((int)ctx->ng, (const float2*)noise_dev, (const float2*)filt_dev, phi_dev, n_samples, n_eta,
+                        (float2*)eta_dev, (float2*)zeta_dev, source_dev, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, double dt, int cheb_deg,
+                         const int8_t* dir_host) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
+    if (batch < 0 || batch > ctx->max_batch || n_steps < 0 || cheb_deg < 1 || (!psi_dev && batch > 0))
+        return fail(ctx, SGW_EINVAL, "bad propagate arguments");
+    if (batch == 0 || n_steps == 0) return SGW_OK;
+    std::vector<cd> c[2];
+    cd ph[2];
+    prop_coeffs(ctx, dt, cheb_deg, c, ph);
+    const std::vector<Step> plan = clenshaw_plan(c, ph, cheb_deg);
+    std::vector<sgw::VecInfo> info(batch, sgw::VecInfo{0, -1, -1, 0});
+    if (dir_host)
+        for (int b = 0; b < batch; ++b) {
+            if (dir_host[b] != 1 && dir_host[b] != -1) return fail(ctx, SGW_EINVAL, "dir must be +1 or -1");
+            info[b].cset = dir_host[b] > 0 ? 0 : 1;
+        }
+    if ((s = upload_info(ctx, info))) return s;
+    float2* psi = (float2*)psi_dev;
+    for (int j = 0; j < n_steps; ++j) {
+        if ((s = run_series(ctx, plan, psi, psi, batch, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps))) return s;
+    }
+    return SGW_OK;
+}
+
+sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* source_dev, int n_samples, int n_eta,
+                            int n_steps, double dt, int cheb_deg, double weight, float* uR_dev) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
+    if (n_samples < 0 || n_eta < 1 || n_steps < 0 || cheb_deg < 1 || 2LL * n_samples * n_eta > ctx->max_batch)
+        return fail(ctx, SGW_EINVAL, "bad TDH arguments (2 n_samples n_eta must be <= max_batch)");
+    if (n_samples == 0) return SGW_OK;
+    if (!eta_dev || !source_dev || !uR_dev) return fail(ctx, SGW_EINVAL, "null TDH pointers");
+    cudaStream_t st = ctx->stream;
+    const int n = ctx->n;
+    const int64_t ng = ctx->ng;
+    const int B = 2 * n_samples * n_eta;
+    const float w = (float)(weight > 0 ? weight : 2.0 / n_eta);
+    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
+    void *p0, *p1, *p2;
+    if ((s = work(ctx, 1, sizeof(float2) * ng * B, &p0))) return s;                 // psi batch
+    if ((s = work(ctx, 2, sizeof(float2) * ng * n_samples, &p1))) return s;         // Poisson planes
+    if ((s = work(ctx, 3, sizeof(float) * ng * n_samples * 4, &p2))) return s;      // vtot, dv, rho0, vp
+    float2* psi = (float2*)p0;
+    float2* Wp = (float2*)p1;
+    float* vtot = (float*)p2;
+    float* dv = vtot + ng * n_samples;
+    float* rho0 = dv + ng * n_samples;
+    float* vp = rho0 + ng * n_samples;
+    // v_p = v_C * source (Poisson, periodic, k = 0 dropped)
+    sgw::launch_real_to_c64(ng * n_samples, source_dev, ctx->B1, st);
+    CKL();
+    sgw::launch_plane_fwd(n, ctx->B1, Wp, n_samples, ctx->tw, st);
+    sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+    sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 2, nullptr, nullptr, nullptr, nullptr, nullptr, 0, vp, st);
+    CKL();
+    // eta pairs: (eta, d eta = -i v_p eta)
+    sgw::launch_kick((int)ng, (const float2*)eta_dev, vp, n_samples, n_eta, psi, st);
+    CKL();
+    std::vector<sgw::VecInfo> info(B);
+    for (int sm = 0; sm < n_samples; ++sm)
+        for (int l = 0; l < 2 * n_eta; ++l) {
+            const int b = sm * 2 * n_eta + l;
+            const bool tan = l >= n_eta;
+            info[b] = sgw::VecInfo{sm, tan ? sm : -1, tan ? b - n_eta : -1, 0};
+        }
+    if ((s = upload_info(ctx, info))) return s;
+    std::vector<cd> c[2];
+    cd ph[2];
+    prop_coeffs(ctx, dt, cheb_deg, c, ph);
+    const std::vector<Step> plan = clenshaw_plan(c, ph, cheb_deg);
+    const int64_t uR_stride = (int64_t)(n_steps + 1) * ng;
+    for (int j = 0; j <= n_steps; ++j) {
+        // H(t_j): density, Poisson of (rho - rho0) + i d rho, potentials and u^R(t_j)
+        sgw::launch_density_fwd(n, psi, n_samples, n_eta, w, rho0, j == 0 ? 1 : 0, Wp, ctx->tw, st);
+        sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+        sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 1, nullptr, ctx->vloc, vtot, dv, uR_dev + (int64_t)j * ng,
+                              uR_stride, nullptr, st);
+        CKL();
+        if (j == n_steps) break;
+        if ((s = run_series(ctx, plan, psi, psi, B, vtot, dv, ctx->info, j > 0, true))) return s;
+    }
+    return SGW_OK;
+}
+
+sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_samples, int n_steps) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 0 || n_steps < 0) return fail(ctx, SGW_EINVAL, "bad time-order arguments");
+    if (n_samples == 0) return SGW_OK;
+    if (!uR_dev || !u_dev) return fail(ctx, SGW_EINVAL, "null time-order pointers");
+    int M = 64;
+    while (M < 4 * (n_steps + 1)) M *= 2;
+    if (M > 4096) return fail(ctx, SGW_EINVAL, "n_steps too large for the time-ordering FFT (M <= 4096)");
+    if (ctx->twM_n != M) {
+        if (ctx->twM) cudaFree(ctx->twM);
+        ctx->twM = nullptr;
+        ctx->twM_n = 0;
+        CK(cudaMalloc(&ctx->twM, sizeof(float2) * M));
+        auto t = twiddles(M);
+        CK(cudaMemcpy(ctx->twM, t.data(), sizeof(float2) * M, cudaMemcpyHostToDevice));
+        ctx->twM_n = M;
+    }
+    sgw::launch_time_order((int)ctx->ng, uR_dev, (float2*)u_dev, n_samples, n_steps, M, ctx->twM, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev, int n_samples, int n_steps,
+                       double dt, int cheb_deg, int fp64_accum, double* sigma_dev) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
+    if (n_samples < 0 || n_steps < 0 || cheb_deg < 1 || 2 * n_samples > ctx->max_batch)
+        return fail(ctx, SGW_EINVAL, "bad sigma arguments (2 n_samples must be <= max_batch)");
+    if (n_samples == 0) return SGW_OK;
+    if (!zeta_dev || !phi_dev || !u_dev || !sigma_dev) return fail(ctx, SGW_EINVAL, "null sigma pointers");
+    cudaStream_t st = ctx->stream;
+    const int64_t ng = ctx->ng;
+    const int B = 2 * n_samples;
+    const int nblk = (int)std::min<int64_t>((ng + 255) / 256, 128);
+    void* p;
+    if ((s = work(ctx, 4, sizeof(double2) * (size_t)n_samples * (n_steps + 1) * 2 * nblk, &p))) return s;
+    double2* partial = (double2*)p;
+    std::vector<cd> c[2];
+    cd ph[2];
+    prop_coeffs(ctx, dt, cheb_deg, c, ph);
+    const std::vector<Step> plan = clenshaw_plan(c, ph, cheb_deg);
+    std::vector<sgw::VecInfo> info(B);
+    for (int sm = 0; sm < n_samples; ++sm) {
+        info[2 * sm] = sgw::VecInfo{0, -1, -1, 1};      // zeta_occ: backwards, e^{+i H t}
+        info[2 * sm + 1] = sgw::VecInfo{0, -1, -1, 0};  // zeta_unocc: forwards
+    }
+    if ((s = upload_info(ctx, info))) return s;
+    float2* z = (float2*)zeta_dev;
+    const int64_t u_ss = (int64_t)(n_steps + 1) * ng;
+    for (int j = 0; j <= n_steps; ++j) {
+        sgw::launch_sigma_accum((int)ng, z, phi_dev, (const float2*)u_dev, n_samples, u_ss, j, n_steps, (float)ctx->dV,
+                                fp64_accum, partial, nblk, st);
+        CKL();
+        if (j == n_steps) break;
+        if ((s = run_series(ctx, plan, z, z, B, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps))) return s;
+    }
+    sgw::launch_sigma_reduce(partial, n_samples, n_steps, nblk, ctx->dV, fp64_accum, sigma_dev, st);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_exchange(sgw_ctx* ctx, const void* eta_dev, const float* phi_dev, int n_samples, int n_eta,
+                        double* x_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 0 || n_eta < 1 || n_eta > ctx->max_batch) return fail(ctx, SGW_EINVAL, "bad exchange arguments");
+    if (n_samples == 0) return SGW_OK;
+    if (!eta_dev || !phi_dev || !x_dev) return fail(ctx, SGW_EINVAL, "null exchange pointers");
+    cudaStream_t st = ctx->stream;
+    const int64_t ng = ctx->ng;
+    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
+    CK(cudaMemsetAsync(x_dev, 0, sizeof(double) * n_samples, st));
+    const int per_call = std::max(1, ctx->max_batch / n_eta);
+    for (int s0 = 0; s0 < n_samples; s0 += per_call) {
+        const int ns = std::min(per_call, n_samples - s0);
+        const int B = ns * n_eta;
+        sgw::launch_scale_mul((int64_t)B * ng, phi_dev, (int)ng, (const float2*)eta_dev + (size_t)s0 * n_eta * ng,
+                              ctx->B1, st);
+        sgw::launch_plane_fwd(ctx->n, ctx->B1, ctx->W, B, ctx->tw, st);
+        // <f|v_C f> = (dV / N) sum_k 4 pi/k^2 |F(k)|^2 ; X = -(1/n_eta) sum_l
+        sgw::launch_pencil_coulomb_energy(ctx->n, ctx->W, B, n_eta, kscale, -ctx->dV / (double)ng / n_eta, ctx->tw,
+                                          x_dev + s0, st);
+        CKL();
+    }
+    return SGW_OK;
+}
+
+sgw_status sgw_sigma_omega(sgw_ctx* ctx, const double* sigma_dev, int n_samples, int n_steps, double dt, double gamma,
+                           const double* omega_dev, int n_omega, int fp64, double* out_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 1 || n_steps < 0 || n_omega < 0 || !sigma_dev || (!omega_dev && n_omega) || (!out_dev && n_omega))
+        return fail(ctx, SGW_EINVAL, "bad sigma-omega arguments");
+    sgw::launch_sigma_omega(sigma_dev, n_samples, n_steps, dt, gamma, omega_dev, n_omega, fp64, out_dev, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_dev, int n_samples, int n_steps,
+                         double dt, double gamma, double eps_ks, double vxc, double window, double step, int fp64,
+                         double* result_host) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 1 || n_steps < 0 || !(window > 0) || !(step > 0) || !sigma_dev || !x_dev || !result_host)
+        return fail(ctx, SGW_EINVAL, "bad QP arguments");
+    const int n_scan = (int)std::llround(2.0 * window / step) + 1;
+    void* p;
+    const size_t bytes = sizeof(double) * (((n_scan + 1) & ~1) + 2 * (2 * n_steps + 1)) + 4 * sizeof(double);
+    if ((s = work(ctx, 5, bytes, &p))) return s;
+    double* scan = (double*)p;
+    double* result = ctx->scal + 16;
+    sgw::launch_qp(sigma_dev, x_dev, n_samples, n_steps, dt, gamma, eps_ks, vxc, window, step, fp64, scan, n_scan,
+                   result, ctx->stream);
+    CKL();
+    CK(cudaMemcpyAsync(result_host, result, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (std::isnan(result_host[0])) return fail(ctx, SGW_ENOCONV, "no sign change of the QP equation in the window");
+    return SGW_OK;
+}
+
+}  // extern "C"

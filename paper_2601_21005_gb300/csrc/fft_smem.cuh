@@ -1,0 +1,139 @@
+// Shared-memory FFT building blocks for sm_103a.
+//
+// Batched complex FFTs of lines held in shared memory, by Stockham mixed-radix stages
+// (radix 8, 4 and 2; Govindaraju et al., "High performance discrete Fourier transforms
+// on graphics processors", SC'08).  Each stage reads its butterflies' inputs into
+// registers, synchronises, and writes the outputs back to the same buffer, so the
+// transform runs in place without a ping-pong buffer.
+//
+// Stage (radix R, current sub-length Ns) for butterfly j in [0, N/R):
+//   k = j mod Ns; v_r = x[j + r N/R] * w^(r k), w = exp(dir 2 pi i / (Ns R));
+//   V = DFT_R(v); y[(j div Ns) Ns R + k + q Ns] = V_q.
+// dir = -1 is the forward transform (e^{-2 pi i jk/N}), +1 the unnormalised inverse.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sgw {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by dir * i  (dir = +-1)
+template <int DIR> __device__ __forceinline__ float2 mul_i(float2 a) {
+    return DIR > 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <int R, int DIR> struct Dft;
+
+template <int DIR> struct Dft<2, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+
+template <int DIR> struct Dft<4, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        float2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        float2 s13 = cadd(v[1], v[3]), d13 = mul_i<DIR>(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    }
+};
+
+template <int DIR> struct Dft<8, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        // split into even / odd radix-4 transforms, combine with w8^q = exp(dir 2 pi i q / 8)
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4, DIR>::run(e);
+        Dft<4, DIR>::run(o);
+        const float r = 0.70710678118654752440f;  // 1/sqrt(2)
+        // w8^1 = (1 + dir i)/sqrt2, w8^2 = dir i, w8^3 = (-1 + dir i)/sqrt2
+        float2 o1 = make_float2(r * (o[1].x - DIR * o[1].y), r * (o[1].y + DIR * o[1].x));
+        float2 o2 = mul_i<DIR>(o[2]);
+        float2 o3 = make_float2(r * (-o[3].x - DIR * o[3].y), r * (-o[3].y + DIR * o[3].x));
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+// Radix of the next stage given the remaining length: 8 while possible, except that
+// 16 splits as 4 x 4 (fewer registers, same passes).
+template <int REM> struct NextRadix {
+    static constexpr int value = (REM == 16) ? 4 : (REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : 2));
+};
+
+// One Stockham stage over NL lines.  Element e of line l is at s[l*LS + e*ES].
+// Consecutive threads take consecutive lines (conflict-free for the layouts used here).
+// tw: table exp(-2 pi i m / N), m < N (read through the read-only cache).
+template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR>
+__device__ __forceinline__ void fft_stage(float2* s, const float2* __restrict__ tw) {
+    constexpr int NB = N / R;
+    constexpr int TOT = NL * NB;
+    constexpr int PER = (TOT + NT - 1) / NT;
+    constexpr int TWS = N / (NS * R);
+    float2 v[PER][R];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * NT;
+        if (TOT % NT == 0 || b < TOT) {
+            const int l = b % NL, j = b / NL;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = s[l * LS + (j + r * NB) * ES];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * NT;
+        if (TOT % NT == 0 || b < TOT) {
+            const int l = b % NL, j = b / NL;
+            const int k = j % NS;
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[(r * k * TWS) & (N - 1)]);
+                    if (DIR > 0) w.y = -w.y;
+                    v[p][r] = cmul(v[p][r], w);
+                }
+            }
+            Dft<R, DIR>::run(v[p]);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) s[l * LS + (base + q * NS) * ES] = v[p][q];
+        }
+    }
+    __syncthreads();
+}
+
+template <int N, int NS, int NL, int LS, int ES, int NT, int DIR>
+__device__ __forceinline__ void fft_rec(float2* s, const float2* __restrict__ tw) {
+    if constexpr (NS < N) {
+        constexpr int R = NextRadix<N / NS>::value;
+        fft_stage<N, R, NS, NL, LS, ES, NT, DIR>(s, tw);
+        fft_rec<N, NS * R, NL, LS, ES, NT, DIR>(s, tw);
+    }
+}
+
+// NL independent N-point FFTs (N a power of two, 2..4096) in shared memory.
+// Caller must __syncthreads() before (data ready); returns after a barrier.
+template <int N, int NL, int LS, int ES, int NT, int DIR>
+__device__ __forceinline__ void fft_lines(float2* s, const float2* __restrict__ tw) {
+    fft_rec<N, 1, NL, LS, ES, NT, DIR>(s, tw);
+}
+
+}  // namespace sgw

@@ -1,0 +1,412 @@
+// Grid kernels of the H.psi path: a periodic n^3 complex grid function is transformed
+// in two passes that each keep their working set on chip:
+//   plane pass  (one CTA per xy plane):  2D FFT of the plane through shared memory;
+//   pencil pass (one CTA per 16 kx-columns x all kz at one ky): FFT along z, the
+//               diagonal k-space multiply, inverse FFT along z.
+// H b = IFFT3(T(k) FFT3(b)) + V b + V_NL b is then
+//   [plane fwd of b] -> [pencil: z fwd, *T/N^3, z inv] -> [plane: xy inv, + V b + V_NL b,
+//   Chebyshev recurrence combine, write; xy fwd of the result for the next term].
+// so one Chebyshev term costs two HBM passes over the batch (Sec. 2.2: the cost of each
+// H application is dominated by the FFTs; the potential multiply is fused into them).
+#include "fft_smem.cuh"
+#include "sgw_internal.cuh"
+
+namespace sgw {
+
+template <int N> struct Cfg {
+    static constexpr int PLANE_NT = N == 16 ? 64 : (N == 32 ? 128 : (N == 64 ? 256 : 512));
+    static constexpr int P = N + 1;   // smem row pitch of a plane (float2), breaks bank conflicts
+    static constexpr int TX = 16;     // pencil tile width along kx (16 x 8 B = 128 B rows)
+    static constexpr int PENCIL_NT = (TX * N / 8) < 64 ? 64 : (TX * N / 8);
+    static constexpr size_t PLANE_SMEM = sizeof(float2) * N * (N + 1);
+    static constexpr size_t PENCIL_SMEM = sizeof(float2) * N * TX;
+};
+
+__device__ __forceinline__ int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
+
+__device__ __forceinline__ float4 ld4(const float2* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float2* p, float2 a, float2 b) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
+// ------------------------------------------------------------------ plane <-> smem
+template <int N, int NT>
+__device__ __forceinline__ void load_plane(float2* sm, const float2* __restrict__ src) {
+    constexpr int P = N + 1;
+    for (int q = threadIdx.x; q < N * N / 2; q += NT) {
+        const int y = q / (N / 2), x = 2 * (q % (N / 2));
+        const float4 v = ld4(src + y * N + x);
+        sm[y * P + x] = make_float2(v.x, v.y);
+        sm[y * P + x + 1] = make_float2(v.z, v.w);
+    }
+}
+
+template <int N, int NT>
+__device__ __forceinline__ void store_plane(float2* __restrict__ dst, const float2* sm) {
+    constexpr int P = N + 1;
+    for (int q = threadIdx.x; q < N * N / 2; q += NT) {
+        const int y = q / (N / 2), x = 2 * (q % (N / 2));
+        st4(dst + y * N + x, sm[y * P + x], sm[y * P + x + 1]);
+    }
+}
+
+template <int N, int NT, int DIR>
+__device__ __forceinline__ void fft2_plane(float2* sm, const float2* __restrict__ tw) {
+    constexpr int P = N + 1;
+    fft_lines<N, N, 1, P, NT, DIR>(sm, tw);   // along y: line = x, element stride = pitch
+    fft_lines<N, N, P, 1, NT, DIR>(sm, tw);   // along x: line = y, element stride = 1
+}
+
+// ------------------------------------------------------------------ forward plane pass
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+k_plane_fwd(const float2* __restrict__ in, float2* __restrict__ W, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int NT = Cfg<N>::PLANE_NT;
+    const size_t plane = ((size_t)blockIdx.y * N + blockIdx.x) * N * N;
+    load_plane<N, NT>(sm, in + plane);
+    __syncthreads();
+    fft2_plane<N, NT, -1>(sm, tw);
+    store_plane<N, NT>(W + plane, sm);
+}
+
+// ------------------------------------------------------------------ pencil pass
+template <int N, int KIND>
+__global__ void __launch_bounds__(Cfg<N>::PENCIL_NT)
+k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int NT = Cfg<N>::PENCIL_NT, TX = Cfg<N>::TX, NXT = N / TX;
+    const int xt = blockIdx.x % NXT, ky = blockIdx.x / NXT;
+    float2* base = W + (size_t)blockIdx.y * N * N * N + (size_t)ky * N + xt * TX;
+    for (int q = threadIdx.x; q < N * TX / 2; q += NT) {
+        const int z = q / (TX / 2), l = 2 * (q % (TX / 2));
+        const float4 v = ld4(base + (size_t)z * N * N + l);
+        sm[z * TX + l] = make_float2(v.x, v.y);
+        sm[z * TX + l + 1] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    fft_lines<N, TX, 1, TX, NT, -1>(sm, tw);
+    const float inv_n3 = 1.0f / ((float)N * N * N);
+    const int my = sfreq(ky, N);
+    for (int q = threadIdx.x; q < N * TX; q += NT) {
+        const int z = q / TX, l = q % TX;
+        const int mx = sfreq(xt * TX + l, N), mz = sfreq(z, N);
+        const float k2 = kscale * (float)(mx * mx + my * my + mz * mz);
+        float f;
+        if (KIND == 0) {
+            f = 0.5f * k2;
+            if (ecut > 0.f) f = fminf(f, ecut);
+        } else {
+            f = k2 > 0.f ? 12.566370614359172f / k2 : 0.f;   // 4 pi / k^2
+        }
+        sm[q] = cscale(sm[q], f * inv_n3);
+    }
+    __syncthreads();
+    fft_lines<N, TX, 1, TX, NT, +1>(sm, tw);
+    for (int q = threadIdx.x; q < N * TX / 2; q += NT) {
+        const int z = q / (TX / 2), l = 2 * (q % (TX / 2));
+        st4(base + (size_t)z * N * N + l, sm[z * TX + l], sm[z * TX + l + 1]);
+    }
+}
+
+// Coulomb energy of the xy-transformed planes: after the z transform F(k) is complete;
+// acc[b / per] += dvn * sum_k 4 pi / k^2 |F(k)|^2 (FP64).
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PENCIL_NT)
+k_pencil_energy(const float2* __restrict__ W, int per, float kscale, double dvn, const float2* __restrict__ tw,
+                double* __restrict__ acc) {
+    extern __shared__ float2 sm[];
+    __shared__ double red[32];
+    constexpr int NT = Cfg<N>::PENCIL_NT, TX = Cfg<N>::TX, NXT = N / TX;
+    const int xt = blockIdx.x % NXT, ky = blockIdx.x / NXT;
+    const float2* base = W + (size_t)blockIdx.y * N * N * N + (size_t)ky * N + xt * TX;
+    for (int q = threadIdx.x; q < N * TX / 2; q += NT) {
+        const int z = q / (TX / 2), l = 2 * (q % (TX / 2));
+        const float4 v = ld4(base + (size_t)z * N * N + l);
+        sm[z * TX + l] = make_float2(v.x, v.y);
+        sm[z * TX + l + 1] = make_float2(v.z, v.w);
+    }
+    __syncthreads();
+    fft_lines<N, TX, 1, TX, NT, -1>(sm, tw);
+    const int my = sfreq(ky, N);
+    double s = 0.0;
+    for (int q = threadIdx.x; q < N * TX; q += NT) {
+        const int z = q / TX, l = q % TX;
+        const int mx = sfreq(xt * TX + l, N), mz = sfreq(z, N);
+        const double k2 = (double)kscale * (double)(mx * mx + my * my + mz * mz);
+        if (k2 > 0.0) {
+            const double a = sm[q].x, b = sm[q].y;
+            s += 12.566370614359172 / k2 * (a * a + b * b);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) atomicAdd(acc + blockIdx.y / per, t * dvn);
+    }
+}
+
+// ------------------------------------------------------------------ fused Chebyshev step
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+k_plane_step(StepArgs a, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    constexpr size_t NG = (size_t)N * N * N;
+    const int z = blockIdx.x, b = blockIdx.y;
+    const size_t plane = ((size_t)b * N + z) * N * N;
+    const VecInfo inf = a.info[b];
+    load_plane<N, NT>(sm, a.W + plane);
+    __syncthreads();
+    fft2_plane<N, NT, +1>(sm, tw);
+
+    const float2 cpsi = a.coef.cpsi[inf.cset], ch = a.coef.ch[inf.cset], c2 = a.coef.c2[inf.cset];
+    const float* V = a.vpot + (size_t)inf.vrow * NG + (size_t)z * N * N;
+    const float* dV = (a.dvpot != nullptr && inf.dvrow >= 0) ? a.dvpot + (size_t)inf.dvrow * NG + (size_t)z * N * N
+                                                                 : nullptr;
+    const float2* bp = (dV != nullptr) ? a.b1 + ((size_t)inf.partner * N + z) * N * N : nullptr;
+    const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
+    const float ebar = a.ebar, alpha = a.alpha;
+    for (int q = threadIdx.x; q < N * N / 2; q += NT) {
+        const int y = q / (N / 2), x = 2 * (q % (N / 2));
+        const int o = y * N + x;
+        float2 h0 = sm[y * P + x], h1 = sm[y * P + x + 1];
+        const float4 bb = ld4(a.b1 + plane + o);
+        const float2 v = __ldg(reinterpret_cast<const float2*>(V + o));
+        h0.x += (v.x - ebar) * bb.x;
+        h0.y += (v.x - ebar) * bb.y;
+        h1.x += (v.y - ebar) * bb.z;
+        h1.y += (v.y - ebar) * bb.w;
+        if (kc != nullptr) {
+            const int g = z * N * N + o;
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e0 = __ldg(a.pt_ptr + g + u), e1 = __ldg(a.pt_ptr + g + u + 1);
+                float2 acc = make_float2(0.f, 0.f);
+                for (int e = e0; e < e1; ++e) {
+                    const int at = __ldg(a.pt_atom + e);
+                    const float4 be = __ldg(a.pt_beta + e);
+                    const float4 c01 = ld4(kc + at * 4);
+                    const float4 c23 = ld4(kc + at * 4 + 2);
+                    acc.x += be.x * c01.x + be.y * c01.z + be.z * c23.x + be.w * c23.z;
+                    acc.y += be.x * c01.y + be.y * c01.w + be.z * c23.y + be.w * c23.w;
+                }
+                if (u == 0) h0 = cadd(h0, acc);
+                else h1 = cadd(h1, acc);
+            }
+        }
+        if (dV != nullptr) {
+            const float2 d = __ldg(reinterpret_cast<const float2*>(dV + o));
+            const float4 pb = ld4(bp + o);
+            h0.x += d.x * pb.x;
+            h0.y += d.x * pb.y;
+            h1.x += d.y * pb.z;
+            h1.y += d.y * pb.w;
+        }
+        float2 o0 = cmul(ch, cscale(h0, alpha)), o1 = cmul(ch, cscale(h1, alpha));
+        if (a.psi != nullptr) {
+            const float4 pp = ld4(a.psi + plane + o);
+            o0 = cadd(o0, cmul(cpsi, make_float2(pp.x, pp.y)));
+            o1 = cadd(o1, cmul(cpsi, make_float2(pp.z, pp.w)));
+        }
+        if (a.b2 != nullptr) {
+            const float4 b2 = ld4(a.b2 + plane + o);
+            o0 = cadd(o0, cmul(c2, make_float2(b2.x, b2.y)));
+            o1 = cadd(o1, cmul(c2, make_float2(b2.z, b2.w)));
+        }
+        st4(a.out + plane + o, o0, o1);
+        sm[y * P + x] = o0;
+        sm[y * P + x + 1] = o1;
+    }
+    if (a.Wout == nullptr) return;
+    __syncthreads();
+    fft2_plane<N, NT, -1>(sm, tw);
+    store_plane<N, NT>(a.Wout + plane, sm);
+}
+
+// ------------------------------------------------------------------ inverse plane pass
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+k_plane_inv(const float2* __restrict__ W, const float2* __restrict__ tw, int mode, float2* out_c,
+            const float* __restrict__ vloc, float* vtot, float* dv, float* uR, int64_t uR_stride, float* out_re) {
+    extern __shared__ float2 sm[];
+    constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    constexpr size_t NG = (size_t)N * N * N;
+    const int z = blockIdx.x, b = blockIdx.y;
+    const size_t plane = ((size_t)b * N + z) * N * N;
+    load_plane<N, NT>(sm, W + plane);
+    __syncthreads();
+    fft2_plane<N, NT, +1>(sm, tw);
+    if (mode == 0) {
+        store_plane<N, NT>(out_c + plane, sm);
+        return;
+    }
+    for (int q = threadIdx.x; q < N * N; q += NT) {
+        const int y = q / N, x = q % N;
+        const size_t g = (size_t)z * N * N + q;
+        const float2 c = sm[y * P + x];
+        if (mode == 1) {
+            vtot[(size_t)b * NG + g] = __ldg(vloc + g) + c.x;
+            dv[(size_t)b * NG + g] = c.y;
+            if (uR != nullptr) uR[(size_t)b * uR_stride + g] = c.y;
+        } else {
+            out_re[(size_t)b * NG + g] = c.x;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ TDH density
+// Sample s owns batch vectors [s*2*n_eta, (s+1)*2*n_eta): eta_l then d eta_l.
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+k_density_fwd(const float2* __restrict__ psi, int n_eta, float weight, float* rho0, int store_rho0,
+              float2* __restrict__ Wp, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    constexpr size_t NG = (size_t)N * N * N;
+    const int z = blockIdx.x, s = blockIdx.y;
+    const size_t zoff = (size_t)z * N * N;
+    for (int q = threadIdx.x; q < N * N / 2; q += NT) {
+        const int y = q / (N / 2), x = 2 * (q % (N / 2));
+        const size_t g = zoff + y * N + x;
+        float r0 = 0.f, r1 = 0.f, d0 = 0.f, d1 = 0.f;
+        for (int l = 0; l < n_eta; ++l) {
+            const float4 e = ld4(psi + ((size_t)s * 2 * n_eta + l) * NG + g);
+            const float4 de = ld4(psi + ((size_t)s * 2 * n_eta + n_eta + l) * NG + g);
+            r0 += e.x * e.x + e.y * e.y;
+            r1 += e.z * e.z + e.w * e.w;
+            d0 += 2.f * (e.x * de.x + e.y * de.y);
+            d1 += 2.f * (e.z * de.z + e.w * de.w);
+        }
+        r0 *= weight; r1 *= weight; d0 *= weight; d1 *= weight;
+        float* rz = rho0 + (size_t)s * NG + g;
+        if (store_rho0) {
+            rz[0] = r0;
+            rz[1] = r1;
+        }
+        sm[y * P + x] = make_float2(r0 - rz[0], d0);
+        sm[y * P + x + 1] = make_float2(r1 - rz[1], d1);
+    }
+    __syncthreads();
+    fft2_plane<N, NT, -1>(sm, tw);
+    store_plane<N, NT>(Wp + ((size_t)s * N + z) * N * N, sm);
+}
+
+// ------------------------------------------------------------------ KB projection
+// kbc[b][4a + p] = E_ap * dV * sum_{r in support(a)} beta_ap(r) b1_b(r)
+__global__ void __launch_bounds__(256)
+k_kb_project(const int64_t* __restrict__ atom_off, const int* __restrict__ sup_idx, const float4* __restrict__ sup_beta,
+             const float4* __restrict__ atom_e, const float2* __restrict__ b1, size_t ng, int n_proj, float dV,
+             float2* __restrict__ kbc) {
+    __shared__ float red[8][8];
+    const int at = blockIdx.x, b = blockIdx.y;
+    const int64_t s0 = atom_off[at], s1 = atom_off[at + 1];
+    const float2* v = b1 + (size_t)b * ng;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const float2 p = __ldg(v + __ldg(sup_idx + s));
+        const float4 be = __ldg(sup_beta + s);
+        acc[0] += be.x * p.x; acc[1] += be.x * p.y;
+        acc[2] += be.y * p.x; acc[3] += be.y * p.y;
+        acc[4] += be.z * p.x; acc[5] += be.z * p.y;
+        acc[6] += be.w * p.x; acc[7] += be.w * p.y;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int i = 0; i < 8; ++i) red[w][i] = acc[i];
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        float t = 0.f;
+        for (int k = 0; k < nw; ++k) t += red[k][threadIdx.x];
+        const float4 e = __ldg(atom_e + at);
+        const int p = threadIdx.x >> 1;
+        const float ep = p == 0 ? e.x : (p == 1 ? e.y : (p == 2 ? e.z : e.w));
+        reinterpret_cast<float*>(kbc + (size_t)b * n_proj + at * 4)[threadIdx.x] = ep * dV * t;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+
+template <int N> static cudaError_t set_attrs() {
+    cudaError_t e = cudaSuccess;
+    const int ps = (int)Cfg<N>::PLANE_SMEM;
+    if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_step<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    if ((e = cudaFuncSetAttribute(k_density_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    return e;
+}
+
+cudaError_t grid_init_attributes(int n) {
+    switch (n) {
+        case 16: return set_attrs<16>();
+        case 32: return set_attrs<32>();
+        case 64: return set_attrs<64>();
+        case 128: return set_attrs<128>();
+    }
+    return cudaErrorInvalidValue;
+}
+
+#define SGW_DISPATCH_N(n, ...)                          \
+    switch (n) {                                        \
+        case 16: { constexpr int N = 16; __VA_ARGS__; } break; \
+        case 32: { constexpr int N = 32; __VA_ARGS__; } break; \
+        case 64: { constexpr int N = 64; __VA_ARGS__; } break; \
+        case 128: { constexpr int N = 128; __VA_ARGS__; } break; \
+        default: break;                                 \
+    }
+
+void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st) {
+    SGW_DISPATCH_N(n, k_plane_fwd<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(in, W, tw));
+}
+
+void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st) {
+    SGW_DISPATCH_N(n, {
+        const dim3 grid((N / Cfg<N>::TX) * N, batch);
+        if (kind == 0)
+            k_pencil<N, 0><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw);
+        else
+            k_pencil<N, 1><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw);
+    });
+}
+
+void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
+                                  const float2* tw, double* acc, cudaStream_t st) {
+    SGW_DISPATCH_N(n, {
+        const dim3 grid((N / Cfg<N>::TX) * N, batch);
+        k_pencil_energy<N><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, per, kscale, dvn, tw, acc);
+    });
+}
+
+void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st) {
+    SGW_DISPATCH_N(n, k_plane_step<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(a, tw));
+}
+
+void launch_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c,
+                      const float* vloc, float* vtot, float* dv, float* uR, int64_t uR_stride, float* out_re,
+                      cudaStream_t st) {
+    SGW_DISPATCH_N(n, k_plane_inv<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
+                              W, tw, mode, out_c, vloc, vtot, dv, uR, uR_stride, out_re));
+}
+
+void launch_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0,
+                        int store_rho0, float2* Wp, const float2* tw, cudaStream_t st) {
+    SGW_DISPATCH_N(n, k_density_fwd<N><<<dim3(N, n_samples), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
+                              psi, n_eta, weight, rho0, store_rho0, Wp, tw));
+}
+
+void launch_kb_project(int n, const KBDev& kb, const float2* b1, int batch, float dV, float2* kbc, cudaStream_t st) {
+    if (kb.n_atoms == 0 || batch == 0) return;
+    const size_t ng = (size_t)n * n * n;
+    k_kb_project<<<dim3(kb.n_atoms, batch), 256, 0, st>>>(kb.atom_off, kb.sup_idx, kb.sup_beta, kb.atom_e, b1, ng,
+                                                         kb.n_proj, dV, kbc);
+}
+
+}  // namespace sgw

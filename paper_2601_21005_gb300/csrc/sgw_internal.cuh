@@ -1,0 +1,107 @@
+// Internal declarations shared by the translation units of libsgw.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sgw {
+
+// Per-vector description for the fused Chebyshev step.
+struct VecInfo {
+    int vrow;     // row of the local potential table used by this vector
+    int dvrow;    // row of the tangent potential (-1: not a tangent vector)
+    int partner;  // batch index of the vector whose b_{k+1} couples through dvrow
+    int cset;     // coefficient set (0 forward / 1 backward)
+};
+
+// Coefficients of one fused step, per coefficient set:
+//   out = cpsi * psi + ch * alpha * (H b1 - ebar b1 [+ dv * b1_partner]) + c2 * b2
+struct StepCoef {
+    float2 cpsi[2];
+    float2 ch[2];
+    float2 c2[2];
+};
+
+struct KBDev {
+    int n_atoms = 0;
+    int n_proj = 0;            // 4 * n_atoms (padded)
+    int64_t n_sup = 0;
+    int* atom_nproj = nullptr;   // [n_atoms]
+    int64_t* atom_off = nullptr; // [n_atoms + 1]
+    int* sup_idx = nullptr;      // [n_sup]
+    float4* sup_beta = nullptr;  // [n_sup]   beta_a0..3 at each support point
+    float4* atom_e = nullptr;    // [n_atoms] E_a0..3
+    // point-major view for the apply
+    int* pt_ptr = nullptr;       // [ng + 1]
+    int* pt_atom = nullptr;      // [n_sup]
+    float4* pt_beta = nullptr;   // [n_sup]
+};
+
+struct StepArgs {
+    const float2* W;        // [B][ng] input planes in the xy-transformed / z-filtered representation
+    float2* Wout;           // [B][ng] forward xy transform of the output (nullptr: skip)
+    const float2* b1;       // [B][ng] real-space vector H acts on
+    const float2* b2;       // [B][ng] real-space b_{k+2} (nullptr when c2 == 0)
+    const float2* psi;      // [B][ng] real-space psi (nullptr when cpsi == 0)
+    float2* out;            // [B][ng] real-space output
+    const float* vpot;      // [rows][ng]
+    const float* dvpot;     // [rows][ng] or nullptr
+    const VecInfo* info;    // [B]
+    const float2* kbc;      // [B][n_proj] E-weighted projector coefficients (nullptr: no KB)
+    const int* pt_ptr;
+    const int* pt_atom;
+    const float4* pt_beta;
+    int n_proj;
+    float ebar, alpha;
+    StepCoef coef;
+};
+
+// ---- grid kernels (kernels_grid.cu)
+bool grid_supported(int n);
+cudaError_t grid_init_attributes(int n);
+void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st);
+// kind: 0 kinetic (T(k)/N^3, capped at ecut if ecut > 0), 1 Coulomb (4 pi/k^2 / N^3, k=0 -> 0)
+void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw,
+                   cudaStream_t st);
+// exchange energy: acc[b / per] += (dV / N) sum_k v(k) |F(k)|^2 after the z transform
+void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
+                                  const float2* tw, double* acc, cudaStream_t st);
+void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st);
+// inverse xy transform of W, epilogue: mode 0 -> out_c[b] = plane (c64);
+// mode 1 (Poisson of TDH densities) -> vtot[b] = vloc + Re, dv[b] = Im, uR[b] = Im (if uR)
+void launch_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c,
+                      const float* vloc, float* vtot, float* dv, float* uR, int64_t uR_stride,
+                      float* out_re, cudaStream_t st);
+void launch_kb_project(int n, const KBDev& kb, const float2* b1, int batch, float dV, float2* kbc,
+                       cudaStream_t st);
+// density of TDH pairs for each sample, packed as (rho - rho0) + i d rho, fwd xy transformed into Wp.
+void launch_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0,
+                        int store_rho0, float2* Wp, const float2* tw, cudaStream_t st);
+
+// ---- other kernels (kernels_misc.cu)
+void launch_noise(int ng, uint64_t seed, uint32_t stream_id, int sample0, int n_samples, int n_vec,
+                  float amp, float2* out, cudaStream_t st);
+void launch_real_to_c64(int64_t count, const float* in, float2* out, cudaStream_t st);
+void launch_kick(int ng, const float2* eta, const float* vp, int n_samples, int n_eta, float2* psi,
+                 cudaStream_t st);
+void launch_scale_mul(int64_t count, const float* phi, int ng, const float2* eta, float2* out, cudaStream_t st);
+// power-iteration helpers (single vector, FP64 reductions into scal[])
+void launch_dot2(int ng, const float2* v, const float2* w, double* scal, cudaStream_t st);
+void launch_power_update(int ng, const float2* w, float2* v, const double* scal, double* est_out,
+                         const double* shift, float dV, cudaStream_t st);
+void launch_sigma_accum(int ng, const float2* zeta, const float* phi, const float2* u, int n_samples,
+                        int64_t u_sample_stride, int j, int n_steps, float dV, int fp64, double2* partial,
+                        int nblk, cudaStream_t st);
+void launch_sigma_reduce(const double2* partial, int n_samples, int n_steps, int nblk, double dV, int fp64,
+                         double* sigma, cudaStream_t st);
+void launch_time_order(int ng, const float* uR, float2* u, int n_samples, int n_steps, int M,
+                       const float2* twM, cudaStream_t st);
+void launch_sigma_omega(const double* sigma, int n_samples, int n_steps, double dt, double gamma,
+                        const double* omega, int n_omega, int fp64, double* out, cudaStream_t st);
+void launch_qp(const double* sigma, const double* x, int n_samples, int n_steps, double dt, double gamma,
+               double eps_ks, double vxc, double window, double step, int fp64, double* scan,
+               int n_scan, double* result, cudaStream_t st);
+int time_order_threads(int M);
+void launch_prepare(int ng, const float2* noise, const float2* filt, const float* phi, int n_samples, int n_eta,
+                    float2* eta, float2* zeta, float* source, cudaStream_t st);
+
+}  // namespace sgw

@@ -1,0 +1,82 @@
+"""Stochastic-GW QP energy through the C ABI (the product path).
+
+The steps of Sec. 2.1 (Fig. 1) for batches of Monte-Carlo samples, each one call into
+libsgw; torch only allocates the device buffers and streams:
+
+  white noise -> gapped filter (Eq. 3) -> split into eta / zeta pair / source ->
+  exchange X (Eq. 6) -> linear-response TDH u^R(t) -> time ordering u(t) ->
+  zeta propagation with Sigma(t) accumulation (Eq. 4, 5) -> ... over batches ... ->
+  Sigma(omega) (Eq. 7) and the QP root (Eq. 6) on the sample means.
+"""
+import numpy as np
+
+from . import sgw as _sgw
+
+
+class Pipeline:
+    def __init__(self, n, h, vloc, kb_atoms, phi, e_homo, e_lumo, n_eta=8, n_steps=200, dt=0.05,
+                 cheb_deg=16, n_cheb=128, samples_per_batch=1, seed=1000, stream_id=1, device=0, ecut=0.0,
+                 spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None):
+        import torch
+        self.torch = torch
+        self.n, self.h, self.ng = n, h, n ** 3
+        self.n_eta, self.n_steps, self.dt, self.cheb_deg = n_eta, n_steps, dt, cheb_deg
+        self.ns = samples_per_batch
+        self.seed, self.stream_id = seed, stream_id
+        self.fp64 = 1 if fp64 else 0
+        self.dev = torch.device('cuda', device)
+        mb = max(self.ns * (n_eta + 1), 2 * self.ns * n_eta, 2 * self.ns)
+        self.ctx = _sgw.Context(n, h, ecut=ecut, max_batch=mb, device=device, stream=stream)
+        vl = torch.as_tensor(np.asarray(vloc, dtype=np.float32).reshape(-1)).to(self.dev)
+        self.ctx.set_potential(vl, kb_atoms)
+        if spectrum is None:
+            (self.emin, self.emax), self.raw_bounds = self.ctx.spectral_bounds(bounds_iter, seed, margin)
+        else:
+            self.emin, self.emax = spectrum
+            self.ctx.set_spectrum(self.emin, self.emax)
+        self.e_homo, self.e_lumo = e_homo, e_lumo
+        if coeffs is None:
+            coeffs = _sgw.sgw_gapped_filter_coeffs(e_homo, e_lumo, self.emin, self.emax, n_cheb)
+        self.coeffs = np.asarray(coeffs, dtype=np.float64)
+        self.phi = torch.as_tensor(np.asarray(phi, dtype=np.float32).reshape(-1)).to(self.dev)
+        ng, ns, N = self.ng, self.ns, n_steps
+        c64, f32 = torch.complex64, torch.float32
+        self.noise = torch.empty(ns * (n_eta + 1), ng, dtype=c64, device=self.dev)
+        self.filt = torch.empty_like(self.noise)
+        self.eta = torch.empty(ns * n_eta, ng, dtype=c64, device=self.dev)
+        self.zeta = torch.empty(2 * ns, ng, dtype=c64, device=self.dev)
+        self.source = torch.empty(ns, ng, dtype=f32, device=self.dev)
+        self.uR = torch.empty(ns, N + 1, ng, dtype=f32, device=self.dev)
+        self.u = torch.empty(ns, N + 1, ng, dtype=c64, device=self.dev)
+
+    @property
+    def gamma(self):
+        """Damping gamma = 3 / (N_tau dt) (Sec. 3: N_tau ~ 3 / (gamma dt))."""
+        return 3.0 / (self.n_steps * self.dt)
+
+    def run_batch(self, sample0, sigma_out, x_out):
+        """Samples sample0 .. sample0 + ns - 1; writes Sigma_i(t) [ns][2N+1] (complex128) and X_i [ns]."""
+        c, ns, ne, N = self.ctx, self.ns, self.n_eta, self.n_steps
+        c.white_noise(self.seed, self.stream_id, sample0, ns, ne + 1, self.noise)
+        c.filter_occupied(self.coeffs, self.noise, self.filt)
+        c.prepare_sample(self.noise, self.filt, self.phi, ns, ne, self.eta, self.zeta, self.source)
+        c.exchange(self.eta, self.phi, ns, ne, x_out)
+        c.tdh_response(self.eta, self.source, ns, ne, N, self.dt, self.cheb_deg, self.uR)
+        c.time_order(self.uR, self.u, ns, N)
+        c.sigma_c(self.zeta, self.phi, self.u, ns, N, self.dt, self.cheb_deg, sigma_out, self.fp64)
+
+    def run(self, n_samples, sample0=0):
+        """Run n_samples (a multiple of the batch size); returns device Sigma [n][2N+1] and X [n]."""
+        t = self.torch
+        nb = (n_samples + self.ns - 1) // self.ns
+        sig = t.empty(nb * self.ns, 2 * self.n_steps + 1, dtype=t.complex128, device=self.dev)
+        xs = t.empty(nb * self.ns, dtype=t.float64, device=self.dev)
+        for b in range(nb):
+            s0 = b * self.ns
+            self.run_batch(sample0 + s0, sig[s0:s0 + self.ns], xs[s0:s0 + self.ns])
+        return sig[:n_samples], xs[:n_samples]
+
+    def qp(self, sigma, x, eps_ks, vxc=0.0, window=2.0, step=1e-3, fp64=None):
+        f = self.fp64 if fp64 is None else (1 if fp64 else 0)
+        return self.ctx.qp_energy(sigma.contiguous(), x.contiguous(), sigma.shape[0], self.n_steps, self.dt,
+                                  self.gamma, eps_ks, vxc, window, step, f)

@@ -1,0 +1,330 @@
+"""GPU parity: every step of the CUDA path, called through the C ABI, against the FP64
+oracle on identical seeded inputs.
+
+Tolerances (max |gpu - oracle| / max |oracle| unless stated), from FP32 arithmetic:
+  * white noise: bit-exact signs (integer Philox words);
+  * H psi: 1e-5 (a 3D FFT pair in FP32 has error ~ log2(N_g) eps_32 ~ 1e-6 of the largest term);
+  * one propagation step: 1e-5 per vector (the stated bar for propagated vectors);
+  * Chebyshev filter of degree N: 2e-6 * N (rounding of N Clenshaw steps, each one H psi);
+  * TDH u^R over n steps and Sigma(t): see each test (errors of the propagated orbitals
+    accumulate linearly in the step count);
+  * FP64 reductions, transform and QP: 1e-10 relative to the oracle given identical inputs.
+"""
+import numpy as np
+import pytest
+
+from oracle import chebyshev as cheb
+from oracle import hamiltonian as ham
+from oracle import sgw as osgw
+from oracle.philox import rademacher_words
+from paper_2601_21005_gb300 import build, synth
+
+import gpu_common as gc
+
+torch = pytest.importorskip('torch')
+pytestmark = pytest.mark.gpu
+
+HA_EV = 27.211386245988
+
+
+@pytest.fixture(scope='module', autouse=True)
+def _built():
+    assert torch.cuda.is_available(), 'GPU tests need CUDA'
+    build.build()
+    from paper_2601_21005_gb300 import sgw
+    sgw.lib()
+
+
+def _sgw():
+    from paper_2601_21005_gb300 import sgw
+    return sgw
+
+
+@pytest.fixture(scope='module')
+def wells16():
+    s = synth.wells()
+    g, kb, w, phis = gc.oracle_eigs(s, 8)
+    return s, g, kb, w, phis
+
+
+@pytest.fixture(scope='module')
+def cluster32():
+    s = gc.small_cluster()
+    g = ham.Grid(s['n'], s['h'])
+    kb = ham.KB(s['kb_atoms'])
+    return s, g, kb
+
+
+def _ctx(s, max_batch, spectrum=None):
+    c = _sgw().Context(s['n'], s['h'], max_batch=max_batch)
+    c.set_potential(gc.to_dev(s['vloc'].ravel(), torch, torch.float32), s['kb_atoms'])
+    if spectrum is not None:
+        c.set_spectrum(*spectrum)
+    return c
+
+
+def _rand_c(shape, seed):
+    r = np.random.default_rng(seed)
+    return r.normal(size=shape) + 1j * r.normal(size=shape)
+
+
+def _oracle_bounds(s, g, kb):
+    h = lambda v: ham.apply_h(v, g, s['vloc'], kb)
+    (lo, hi), _ = cheb.spectral_bounds(h, _rand_c(g.shape(), 99), 200, g.dot)
+    return lo, hi
+
+
+# ------------------------------------------------------------------ S1 noise
+def test_white_noise_bitexact():
+    s = gc.small_cluster()
+    c = _ctx(s, 8)
+    ng = s['n'] ** 3
+    out = torch.empty(2 * 3, ng, dtype=torch.complex64, device='cuda')
+    c.white_noise(77, 5, 3, 2, 3, out)
+    got = out.cpu().numpy()
+    amp = np.float32(1 / np.sqrt(s['h'] ** 3))
+    for si in range(2):
+        for v in range(3):
+            ref = rademacher_words(77, 5, 3 + si, v, ng)
+            row = got[si * 3 + v]
+            assert np.array_equal(np.sign(row.real).astype(np.int8), ref)
+            assert np.all(np.abs(row.real) == amp) and np.all(row.imag == 0)
+
+
+# ------------------------------------------------------------------ S3 / S3b H psi
+@pytest.mark.parametrize('which', ['wells16', 'cluster32'])
+def test_apply_h_parity(which, wells16, cluster32):
+    if which == 'wells16':
+        s, g, kb = wells16[0], wells16[1], None
+    else:
+        s, g, kb = cluster32
+    B = 3
+    x = _rand_c((B,) + g.shape(), 1)
+    c = _ctx(s, B)
+    xd = gc.to_dev(x.reshape(B, -1), torch, torch.complex64)
+    yd = torch.empty_like(xd)
+    c.apply_h(xd, yd)
+    ref = ham.apply_h(x.astype(np.complex64).astype(np.complex128), g, s['vloc'], kb)
+    got = yd.cpu().numpy().reshape(ref.shape)
+    for b in range(B):
+        assert gc.rel_err(got[b], ref[b]) < 1e-5
+
+
+def test_apply_h_batch_is_vectorwise(cluster32):
+    """A ragged batch gives the same vectors as one-at-a-time application."""
+    s, g, kb = cluster32
+    x = gc.to_dev(_rand_c((5, g.ng), 2), torch, torch.complex64)
+    c = _ctx(s, 5)
+    y = torch.empty_like(x)
+    c.apply_h(x, y)
+    for b in (0, 4):
+        y1 = torch.empty_like(x[b:b + 1])
+        c.apply_h(x[b:b + 1].contiguous(), y1)
+        assert torch.equal(y1[0], y[b])
+
+
+# ------------------------------------------------------------------ S2 spectral bounds
+def test_spectral_bounds_parity(wells16):
+    s, g = wells16[0], wells16[1]
+    c = _ctx(s, 2)
+    (lo, hi), (rlo, rhi) = c.spectral_bounds(120, 11, 0.05)
+    v0 = osgw.white_noise(g, 11, 0xB0B0, 0, 1)[0].astype(np.complex128)
+    h = lambda v: ham.apply_h(v, g, s['vloc'], None)
+    (olo, ohi), (orlo, orhi) = cheb.spectral_bounds(h, v0, 120, g.dot, 0.05)
+    width = orhi - orlo
+    assert abs(rhi - orhi) < 1e-4 * width
+    assert abs(rlo - orlo) < 1e-4 * width
+    assert abs(lo - olo) < 2e-4 * width and abs(hi - ohi) < 2e-4 * width
+    # bounds enclose the computed spectrum
+    assert lo < wells16[3][0]
+
+
+# ------------------------------------------------------------------ S4 filter
+@pytest.mark.parametrize('which,N,B', [('wells16', 128, 9), ('cluster32', 200, 5)])
+def test_filter_parity(which, N, B, wells16, cluster32):
+    if which == 'wells16':
+        s, g, kb = wells16[0], wells16[1], None
+        w = wells16[3]
+        eh, el = w[3], w[4]
+    else:
+        s, g, kb = cluster32
+        eh, el = -0.3, -0.1
+    lo, hi = _oracle_bounds(s, g, kb)
+    a = cheb.gapped_filter_coeffs(eh, el, lo, hi, N)
+    c = _ctx(s, B, (lo, hi))
+    noise = torch.empty(B, g.ng, dtype=torch.complex64, device='cuda')
+    c.white_noise(5, 1, 0, 1, B, noise)
+    out = torch.empty_like(noise)
+    c.filter_occupied(a, noise, out)
+    ref = cheb.filter_occupied(lambda v: ham.apply_h(v, g, s['vloc'], kb),
+                               osgw.white_noise(g, 5, 1, 0, B).astype(np.complex128), a, lo, hi)
+    got = out.cpu().numpy().reshape(ref.shape)
+    for b in range(B):
+        assert gc.rel_err(got[b], ref[b]) < 2e-6 * N
+    # in place gives the same
+    c.filter_occupied(a, noise, noise)
+    assert torch.equal(noise, out)
+
+
+# ------------------------------------------------------------------ S5 propagator
+def test_propagate_parity(cluster32):
+    s, g, kb = cluster32
+    lo, hi = _oracle_bounds(s, g, kb)
+    B = 5
+    x = _rand_c((B,) + g.shape(), 3)
+    x /= np.sqrt(np.sum(np.abs(x) ** 2, axis=(1, 2, 3), keepdims=True))
+    dirs = np.array([1, -1, 1, -1, 1], dtype=np.int8)
+    c = _ctx(s, B, (lo, hi))
+    h = lambda v: ham.apply_h(v, g, s['vloc'], kb)
+    xd = gc.to_dev(x.reshape(B, -1), torch, torch.complex64)
+    ref = x.astype(np.complex64).astype(np.complex128)
+    for nsteps, tol in ((1, 1e-5), (19, 2e-5 * 20)):
+        c.propagate(xd, nsteps, 0.05, 16, dirs)
+        for b in range(B):
+            for _ in range(nsteps):
+                ref[b] = cheb.propagate_step(h, ref[b], lo, hi, 0.05 * dirs[b], 16)
+        got = xd.cpu().numpy().reshape(ref.shape)
+        for b in range(B):
+            assert gc.rel_err(got[b], ref[b]) < tol, (nsteps, b)
+            # unitary in FP32
+            assert abs(np.linalg.norm(got[b]) - np.linalg.norm(ref[b])) < 1e-5 * np.linalg.norm(ref[b])
+
+
+# ------------------------------------------------------------------ S6/S7 TDH
+def test_tdh_parity(wells16):
+    s, g, kb, w, phis = wells16
+    lo, hi = _oracle_bounds(s, g, None)
+    n_s, n_eta, N = 2, 4, 20
+    prob = osgw.Problem(g, s['vloc'], None, lo, hi, w[3], w[4], phis[3])
+    a = cheb.gapped_filter_coeffs(w[3], w[4], lo, hi, 128)
+    eta = np.stack([osgw.filter_batch(prob, osgw.white_noise(g, 9, 2, si, n_eta + 1), a)[1:] for si in range(n_s)])
+    src = np.stack([osgw.white_noise(g, 9, 2, si, 1)[0] * phis[3] for si in range(n_s)])
+    eta32 = eta.astype(np.complex64)
+    src32 = src.astype(np.float32)
+    c = _ctx(s, 2 * n_s * n_eta, (lo, hi))
+    uR = torch.empty(n_s, N + 1, g.ng, dtype=torch.float32, device='cuda')
+    c.tdh_response(gc.to_dev(eta32.reshape(n_s * n_eta, -1), torch, torch.complex64),
+                   gc.to_dev(src32.reshape(n_s, -1), torch, torch.float32), n_s, n_eta, N, 0.05, 16, uR)
+    got = uR.cpu().numpy().reshape((n_s, N + 1) + g.shape())
+    for si in range(n_s):
+        ref = osgw.tdh_response_tangent(prob, eta32[si].astype(np.complex128), src32[si].astype(np.float64), N, 0.05, 16)
+        assert np.max(np.abs(got[si, 0])) < 1e-5 * np.max(np.abs(ref))     # u^R(0) = 0
+        assert gc.rel_err(got[si], ref) < 2e-4
+
+
+# ------------------------------------------------------------------ S8 time ordering
+def test_time_order_parity():
+    s = gc.small_cluster()
+    n_s, N = 2, 37                     # ragged step count: M = 256
+    r = np.random.default_rng(4)
+    ng = s['n'] ** 3
+    uR = r.normal(size=(n_s, N + 1, ng)).astype(np.float32)
+    c = _ctx(s, 2)
+    u = torch.empty(n_s, N + 1, ng, dtype=torch.complex64, device='cuda')
+    c.time_order(gc.to_dev(uR, torch, torch.float32), u, n_s, N)
+    got = u.cpu().numpy()
+    for si in range(n_s):
+        ref = osgw.time_order(uR[si].astype(np.float64))
+        assert gc.rel_err(got[si], ref) < 2e-6
+
+
+# ------------------------------------------------------------------ S9 zeta + Sigma(t)
+@pytest.mark.parametrize('fp64', [1, 0])
+def test_sigma_c_parity(cluster32, fp64):
+    s, g, kb = cluster32
+    lo, hi = _oracle_bounds(s, g, kb)
+    n_s, N = 2, 15
+    zeta = _rand_c((n_s, 2) + g.shape(), 5).astype(np.complex64)
+    u = (0.3 * _rand_c((n_s, N + 1) + g.shape(), 6)).astype(np.complex64)
+    phi = synth.smooth_orbital(g.n, g.h, (8.0, 8.0, 8.0)).astype(np.float32)
+    c = _ctx(s, 2 * n_s, (lo, hi))
+    zd = gc.to_dev(zeta.reshape(2 * n_s, -1), torch, torch.complex64)
+    sig = torch.empty(n_s, 2 * N + 1, dtype=torch.complex128, device='cuda')
+    c.sigma_c(zd, gc.to_dev(phi.ravel(), torch, torch.float32), gc.to_dev(u.reshape(n_s, N + 1, -1), torch, torch.complex64),
+              n_s, N, 0.05, 16, sig, fp64)
+    got = sig.cpu().numpy()
+    prob = osgw.Problem(g, s['vloc'], kb, lo, hi, 0, 0, phi.astype(np.float64))
+    for si in range(n_s):
+        ref = osgw.sigma_t(prob, zeta[si, 0].astype(np.complex128), zeta[si, 1].astype(np.complex128),
+                           u[si].astype(np.complex128), N, 0.05, 16)
+        assert gc.rel_err(got[si], ref) < (2e-4 if fp64 else 1e-3)
+
+
+# ------------------------------------------------------------------ S10 exchange
+def test_exchange_parity(wells16):
+    s, g, kb, w, phis = wells16
+    n_s, n_eta = 3, 4
+    eta = (_rand_c((n_s, n_eta) + g.shape(), 7) * 0.1).astype(np.complex64)
+    phi = phis[3].astype(np.float32)
+    c = _ctx(s, n_eta * 2)
+    x = torch.empty(n_s, dtype=torch.float64, device='cuda')
+    c.exchange(gc.to_dev(eta.reshape(n_s * n_eta, -1), torch, torch.complex64), gc.to_dev(phi.ravel(), torch, torch.float32),
+               n_s, n_eta, x)
+    prob = osgw.Problem(g, s['vloc'], None, 0, 1, 0, 0, phi.astype(np.float64))
+    for si in range(n_s):
+        ref = osgw.exchange(prob, eta[si].astype(np.complex128))
+        assert abs(x[si].item() - ref) < 1e-5 * abs(ref)
+
+
+# ------------------------------------------------------------------ S11 transform + QP
+def _synthetic_sigma(n_s, N, dt, seed):
+    r = np.random.default_rng(seed)
+    t = dt * np.arange(-N, N + 1)
+    out = []
+    for _ in range(n_s):
+        a, e1, e2 = 0.02 * (1 + 0.3 * r.normal()), -0.4 + 0.02 * r.normal(), 0.3 + 0.02 * r.normal()
+        sp = -1j * a * np.exp(-1j * e2 * t) * (t > 0)
+        sm = 1j * a * np.exp(-1j * e1 * t) * (t < 0)
+        s0 = np.where(t == 0, 0.5 * (-1j * a + 1j * a), 0)
+        out.append(sp + sm + s0)
+    return np.array(out)
+
+
+@pytest.mark.parametrize('fp64', [1, 0])
+def test_sigma_omega_and_qp_parity(fp64):
+    N, dt = 200, 0.05
+    gamma = 3.0 / (N * dt)
+    n_s = 6
+    S = _synthetic_sigma(n_s, N, dt, 8)
+    X = -0.05 + 0.01 * np.random.default_rng(9).normal(size=n_s)
+    s = gc.small_cluster()
+    c = _ctx(s, 2)
+    sd = gc.to_dev(S, torch, torch.complex128)
+    om = np.linspace(-1.0, 1.0, 41)
+    out = torch.empty(41, dtype=torch.complex128, device='cuda')
+    c.sigma_omega(sd, n_s, N, dt, gamma, gc.to_dev(om, torch, torch.float64), out, fp64)
+    ref = osgw.sigma_omega(S.mean(axis=0), dt, gamma, om)
+    assert gc.rel_err(out.cpu().numpy(), ref) < (1e-12 if fp64 else 2e-5)
+    res = c.qp_energy(sd, gc.to_dev(X, torch, torch.float64), n_s, N, dt, gamma, -0.25, 0.0, 2.0, 1e-3, fp64)
+    e, se = osgw.qp_energy(list(S), list(X), dt, gamma, -0.25)
+    assert abs(res['eps_qp'] - e) < (1e-9 if fp64 else 1e-5)
+    assert abs(res['se'] - se) < (1e-9 if fp64 else 1e-5)
+
+
+# ------------------------------------------------------------------ whole path, tiny config
+def test_pipeline_tiny_qp_parity(wells16):
+    """16^3 wells, 16 stochastic orbitals (8 eta pairs), filter degree 128, 200 steps of
+    dt = 0.05 with Chebyshev degree 16: GPU Sigma(t) and QP energy vs the oracle at equal seeds."""
+    from paper_2601_21005_gb300.pipeline import Pipeline
+    s, g, kb, w, phis = wells16
+    lo, hi = _oracle_bounds(s, g, None)
+    a = cheb.gapped_filter_coeffs(w[3], w[4], lo, hi, 128)
+    phi = phis[3]
+    n_samples, n_eta, N, dt = 2, 8, 200, 0.05
+    pl = Pipeline(s['n'], s['h'], s['vloc'], [], phi, w[3], w[4], n_eta=n_eta, n_steps=N, dt=dt, cheb_deg=16,
+                  samples_per_batch=n_samples, seed=1000, stream_id=1, spectrum=(lo, hi), coeffs=a)
+    sig, xs = pl.run(n_samples)
+    prob = osgw.Problem(g, s['vloc'], None, lo, hi, w[3], w[4], phi.astype(np.float32).astype(np.float64))
+    refs, xr = [], []
+    for i in range(n_samples):
+        sr, x, _ = osgw.run_sample(prob, a, 1000, 1, i, n_eta, N, dt, 16)
+        refs.append(sr)
+        xr.append(x)
+    got = sig.cpu().numpy()
+    for i in range(n_samples):
+        assert gc.rel_err(got[i], refs[i]) < 5e-3
+        assert abs(xs[i].item() - xr[i]) < 1e-5 * abs(xr[i])
+    eps_ks = w[3]
+    res = pl.qp(sig, xs, eps_ks)
+    e, se = osgw.qp_energy(refs, xr, dt, pl.gamma, eps_ks)
+    assert abs(res['eps_qp'] - e) * HA_EV < 0.01
