@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the stochastic-GW hot path on one node (one process per GPU).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
+
+One step = one pass of the whole hot path over one batch of Monte-Carlo samples of the
+workload: white noise, gapped filter (Eq. 3), exchange, linear-response TDH (u^R), time
+ordering, zeta propagation with the Sigma(t) accumulation (Eq. 4-5), and the QP solve
+(Eq. 6-7) on the samples accumulated so far.  Default workload: the 64^3 Si35H36 cluster
+(h = 0.5 bohr, 176 electrons), 4 samples x 16 orbitals (8 eta pairs) = 64 orbitals
+propagated for 400 steps of dt = 0.05 with Chebyshev degree 16, filter degree 2000.
+
+The metric counts grid points x propagated orbitals x time steps of the TDH propagation
+per second of the whole step.  With --impl reference the FP64 CPU oracle is timed on a
+bounded sample of the same workload instead (see `oracle_sample`).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = 'grid-pt*orbital*steps/s and time to +/-0.03 eV QP energy, chosen vs plain form'
+UNIT = 'grid-pt*orbital*steps/s'
+HA_EV = 27.211386245988
+
+CONFIGS = {
+    # the 64^3 cluster the metric is quoted on
+    'si35h36_64': dict(system='si_cluster', n=64, h=0.5, radius=10.5, samples_per_batch=4, n_eta=8,
+                       n_steps=400, dt=0.05, cheb_deg=16, n_cheb=2000, workload='Si35H36 cluster, 64^3 grid '
+                       'h=0.5 bohr, 176 electrons, 64 orbitals (4 MC samples x 8 eta pairs) x 400 steps'),
+    # the tiny periodic case (parity-test size)
+    'wells16': dict(system='wells', n=16, h=0.6, samples_per_batch=1, n_eta=8, n_steps=200, dt=0.05,
+                    cheb_deg=16, n_cheb=128, workload='6 Gaussian wells, 16^3 grid h=0.6 bohr, 8 electrons, '
+                    '16 orbitals x 200 steps'),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d['hbm_gbs']), bf16_tflops=float(d['bf16_tflops']), source='measured')
+    return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source='fallback')
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+         'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+         'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix='.csv')
+        os.close(fd)
+        try:
+            self.f = open(self.path, 'w')
+            self.proc = subprocess.Popen(['nvidia-smi', '-i', str(self.device), '--query-gpu=' + self.Q,
+                                          '--format=csv,noheader,nounits', '-lms', '200'],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=['nvidia-smi unavailable'])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(',')]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=['no samples'])
+        sm = [float(r[1]) for r in rows if r[1].replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace('.', '').isdigit()]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == 'active'})
+        pw = [float(r[3]) for r in rows if r[3].replace('.', '').isdigit()]
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=reasons, samples=len(rows), power_w_max=max(pw) if pw else None)
+
+
+# ---------------------------------------------------------------- workload setup (untimed)
+def build_system(cfg):
+    from paper_2601_21005_gb300 import synth
+    if cfg['system'] == 'wells':
+        return synth.wells(n=cfg['n'], h=cfg['h'])
+    return synth.si_cluster(n=cfg['n'], h=cfg['h'], radius=cfg['radius'])
+
+
+def kohn_sham_inputs(cfg, sysd, device):
+    """E_HOMO, E_LUMO and the HOMO orbital (the preliminary-DFT inputs of Sec. 2.1) from a GPU
+    subspace iteration through libsgw, plus the spectral interval by shifted power iteration."""
+    import torch
+    from paper_2601_21005_gb300 import sgw
+    from paper_2601_21005_gb300.eigensolver import lowest_states
+    n_occ = sysd['n_occ']
+    extra = max(8, n_occ // 4)
+    ctx = sgw.Context(cfg['n'], cfg['h'], max_batch=n_occ + 1 + extra, device=device)
+    vl = torch.as_tensor(sysd['vloc'].reshape(-1).astype('float32')).cuda(device)
+    ctx.set_potential(vl, sysd['kb_atoms'])
+    (emin, emax), raw = ctx.spectral_bounds(200, cfg.get('seed', 1000), 0.05)
+    w, phis, res = lowest_states(ctx, n_occ + 1, emin, emax, extra=extra)
+    ctx.close()
+    return dict(e_homo=float(w[n_occ - 1]), e_lumo=float(w[n_occ]), phi=phis[n_occ - 1], emin=emin, emax=emax,
+                raw_bounds=raw, eig_residual=res)
+
+
+def make_pipeline(cfg, sysd, ks, device, seed, fp64=True):
+    from paper_2601_21005_gb300.pipeline import Pipeline
+    return Pipeline(cfg['n'], cfg['h'], sysd['vloc'], sysd['kb_atoms'], ks['phi'], ks['e_homo'], ks['e_lumo'],
+                    n_eta=cfg['n_eta'], n_steps=cfg['n_steps'], dt=cfg['dt'], cheb_deg=cfg['cheb_deg'],
+                    n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'], seed=seed, stream_id=1,
+                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64)
+
+
+def units_per_step(cfg):
+    """grid points x TDH-propagated orbitals x time steps of one batch."""
+    return cfg['n'] ** 3 * 2 * cfg['n_eta'] * cfg['samples_per_batch'] * cfg['n_steps']
+
+
+def roofline(prof, peaks):
+    """Dominant kernel kind by device time; achieved = its algorithmic bytes / its event time."""
+    kinds = {k: v for k, v in prof.items() if v['launches'] > 0 and v['alg_bytes'] > 0}
+    total = sum(v['ms'] for v in prof.values())
+    name = max(kinds, key=lambda k: kinds[k]['ms'])
+    v = kinds[name]
+    gbs = v['alg_bytes'] / (v['ms'] * 1e-3) / 1e9
+    peak = peaks['hbm_gbs']
+    shares = {k: round(x['ms'] / total, 4) for k, x in prof.items() if x['launches']}
+    return dict(bound='hbm', achieved=round(gbs, 1), peak=peak, unit='GB/s', frac=round(gbs / peak, 4),
+                traffic=None, kernel=name, launches=v['launches'], avg_launch_us=round(1e3 * v['ms'] / v['launches'], 2),
+                alg_bytes_per_launch=round(v['alg_bytes'] / v['launches']), peak_source=peaks['source'] + ' hbm_gbs',
+                time_shares=shares,
+                other_kernels={k: round(x['alg_bytes'] / (x['ms'] * 1e-3) / 1e9, 1) for k, x in kinds.items()})
+
+
+def time_to_target(pl, sig, xs, eps_ks, seconds_per_sample, target_ev=0.03):
+    """Samples needed for a QP standard error of target_ev, from the per-sample spread so far."""
+    r = pl.qp(sig, xs, eps_ks)
+    n = sig.shape[0]
+    se_ev = r['se'] * HA_EV
+    per_sample_ev = se_ev * n ** 0.5
+    need = max(1.0, (per_sample_ev / target_ev) ** 2)
+    return dict(seconds=round(need * seconds_per_sample, 3), samples_needed=round(need, 1),
+                per_sample_std_eV=round(per_sample_ev, 4), qp_eV=round(r['eps_qp'] * HA_EV, 5),
+                se_eV=round(se_ev, 5), z=round(r['z'], 4), n_samples_used=n)
+
+
+# ---------------------------------------------------------------- the oracle on the host cores
+def oracle_sample(cfg, n_filter_terms=2, n_tdh_steps=1, n_zeta_steps=1, seed=1000):
+    """Time the FP64 oracle on a bounded sample of one batch and extrapolate to the batch.
+
+    Timed pieces (one MC sample): n_filter_terms Chebyshev terms of the filter on the
+    n_eta + 1 noise vectors, n_tdh_steps TDH steps of the n_eta pairs, n_zeta_steps zeta
+    steps of the pair with the Sigma(t) sums, the exchange, and the time ordering of a
+    4096-point slice of u^R over the full step count.  The batch time is
+      n_samples * (N_chb t_filter + N_tau (t_tdh + t_zeta) + t_x + t_to * N_g / 4096).
+    Inputs are the workload's system with a smooth stand-in orbital (timing does not depend
+    on the orbital's values).
+    """
+    import numpy as np
+    from oracle import chebyshev as cheb
+    from oracle import hamiltonian as ham
+    from oracle import sgw as osgw
+    from paper_2601_21005_gb300 import synth
+    sysd = build_system(cfg)
+    g = ham.Grid(cfg['n'], cfg['h'])
+    kb = ham.KB(sysd['kb_atoms']) if sysd['kb_atoms'] else None
+    L = cfg['n'] * cfg['h']
+    phi = synth.smooth_orbital(cfg['n'], cfg['h'], (L / 2, L / 2, L / 2))
+    emin, emax = float(sysd['vloc'].min()) - 1.0, 0.5 * 3 * (np.pi / cfg['h']) ** 2 + 1.0
+    prob = osgw.Problem(g, sysd['vloc'], kb, emin, emax, emin + 0.5, emin + 0.6, phi)
+    ne, N = cfg['n_eta'], cfg['n_steps']
+    t = {}
+    noise = osgw.white_noise(g, seed, 1, 0, ne + 1)
+    t0 = time.perf_counter()
+    filt = osgw.filter_batch(prob, noise, np.ones(n_filter_terms + 1) / (n_filter_terms + 1))
+    t['filter_term'] = (time.perf_counter() - t0) / n_filter_terms
+    eta, zbar = filt[1:], noise[0]
+    t0 = time.perf_counter()
+    osgw.tdh_response_tangent(prob, eta, zbar * phi, n_tdh_steps, cfg['dt'], cfg['cheb_deg'])
+    t['tdh_step'] = (time.perf_counter() - t0) / n_tdh_steps
+    u = np.zeros((n_zeta_steps + 1,) + g.shape(), dtype=np.complex128)
+    t0 = time.perf_counter()
+    osgw.sigma_t(prob, filt[0], zbar - filt[0], u, n_zeta_steps, cfg['dt'], cfg['cheb_deg'])
+    t['zeta_step'] = (time.perf_counter() - t0) / n_zeta_steps
+    t0 = time.perf_counter()
+    osgw.exchange(prob, eta)
+    t['exchange'] = time.perf_counter() - t0
+    sl = min(4096, g.ng)
+    t0 = time.perf_counter()
+    osgw.time_order(np.zeros((N + 1, sl)))
+    t['time_order'] = (time.perf_counter() - t0) * g.ng / sl
+    per_sample = (cfg['n_cheb'] * t['filter_term'] + N * (t['tdh_step'] + t['zeta_step']) + t['exchange']
+                  + t['time_order'])
+    batch_s = cfg['samples_per_batch'] * per_sample
+    measured = n_filter_terms * t['filter_term'] + n_tdh_steps * t['tdh_step'] + n_zeta_steps * t['zeta_step'] \
+        + t['exchange'] + t['time_order'] * sl / g.ng
+    return dict(value=units_per_step(cfg) / batch_s, batch_seconds=batch_s, measured_seconds=measured, parts=t)
+
+
+def run_reference(args, cfg):
+    """--impl reference: the FP64 oracle on the host cores (rank 0 only), K timed bounded samples."""
+    rank = int(os.environ.get('RANK', '0'))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample(cfg)
+    vals, meas = [], []
+    for _ in range(args.steps):
+        r = oracle_sample(cfg)
+        vals.append(r['value'])
+        meas.append(r['measured_seconds'])
+    v = statistics.median(vals)
+    sample = ('per step: 1 MC sample of %s -- %d filter terms on %d vectors, 1 TDH step of %d pairs, '
+              '1 zeta step, exchange, time ordering of a 4096-point slice; extrapolated to the batch of %d '
+              'samples x (N_chb=%d, N_tau=%d)' % (cfg['workload'], 2, cfg['n_eta'] + 1, cfg['n_eta'],
+                                                  cfg['samples_per_batch'], cfg['n_cheb'], cfg['n_steps']))
+    line = dict(impl='reference', metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1e3 * statistics.median(meas), higher_is_better=True,
+                scaling='weak', vs_baseline=None, dtype='f64', data='synthetic',
+                config=dict(workload=cfg['workload'], l2='inputs larger than L2'),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind='oracle', sample=sample,
+                                  batch_seconds_extrapolated=r['batch_seconds'], parts_s=r['parts']),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def cpu_baseline_subprocess(args):
+    """Run the reference arm once (one bounded sample) in a fresh process with one BLAS thread."""
+    env = dict(os.environ, OMP_NUM_THREADS='1', OPENBLAS_NUM_THREADS='1', MKL_NUM_THREADS='1')
+    for k in ('RANK', 'WORLD_SIZE', 'LOCAL_RANK'):
+        env.pop(k, None)
+    cmd = [sys.executable, os.path.join(ROOT, 'bench.py'), '--impl', 'reference', '--steps', '1', '--warmup', '0',
+           '--config', args.config]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    for line in r.stdout.splitlines()[::-1]:
+        if line.startswith('{'):
+            return json.loads(line)['cpu_baseline']
+    return dict(value=None, unit=UNIT, cores=1, kind='oracle', sample='failed: ' + r.stderr[-300:])
+
+
+def run_ours(args, cfg):
+    import numpy as np
+    import torch
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local))
+    from paper_2601_21005_gb300 import build
+    build.build()
+    peaks = load_peaks()
+    seed = 1000 * 2
+    sysd = build_system(cfg)
+    t_setup = time.perf_counter()
+    ks = kohn_sham_inputs(cfg, sysd, local)
+    pl = make_pipeline(cfg, sysd, ks, local, seed)
+    t_setup = time.perf_counter() - t_setup
+    ns = cfg['samples_per_batch']
+    nb_total = args.warmup + args.steps
+    sig = torch.empty(nb_total * ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
+    xs = torch.empty(nb_total * ns, dtype=torch.float64, device='cuda')
+    base = rank * 1000000          # each rank draws its own samples: no data-path collective
+    eps_ks = ks['e_homo']
+
+    def step(b):
+        s0 = b * ns
+        pl.run_batch(base + s0, sig[s0:s0 + ns], xs[s0:s0 + ns])
+        pl.qp(sig[:s0 + ns], xs[:s0 + ns], eps_ks) if s0 + ns >= 2 else None
+
+    for b in range(args.warmup):
+        step(b)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    pl.ctx.profile(True)
+    n0 = pl.ctx.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for b in range(args.warmup, nb_total):
+        step(b)
+    e1.record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = pl.ctx.launch_count() - n0
+    prof = pl.ctx.profile_read()
+    pl.ctx.profile(False)
+    if dist:
+        t = torch.tensor([ms], device='cuda', dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = units_per_step(cfg) * args.steps * world / (ms * 1e-3)
+    tt = time_to_target(pl, sig, xs, eps_ks, ms_per_step * 1e-3 / ns)
+
+    # end to end through the public API: per step the target orbital comes from pinned host
+    # memory and Sigma(t), X and the QP result go back to the host
+    phi_h = torch.from_numpy(np.asarray(ks['phi'], dtype=np.float32).reshape(-1)).pin_memory()
+    sig_h = torch.empty(ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128).pin_memory()
+    x_h = torch.empty(ns, dtype=torch.float64).pin_memory()
+    sig_e = torch.empty(ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
+    x_e = torch.empty(ns, dtype=torch.float64, device='cuda')
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for b in range(args.steps):
+        pl.phi.copy_(phi_h, non_blocking=True)
+        pl.run_batch(base + 500000 + b * ns, sig_e, x_e)
+        sig_h.copy_(sig_e, non_blocking=True)
+        x_h.copy_(x_e, non_blocking=True)
+        pl.qp(sig_e, x_e, eps_ks)           # returns host scalars (synchronises)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_e2e], device='cuda', dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = dict(value=units_per_step(cfg) * args.steps * world / (ms_e2e * 1e-3), unit=UNIT,
+               h2d_bytes_per_step=phi_h.numel() * 4, d2h_bytes_per_step=sig_h.numel() * 16 + x_h.numel() * 8 + 32)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    rl = roofline(prof, peaks)
+    cpu = cpu_baseline_subprocess(args) if world == 1 and not args.no_cpu_baseline else None
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=ms_per_step, higher_is_better=True, scaling='weak', vs_baseline=None, dtype='c64/f32 + f64',
+                data='synthetic',
+                config=dict(workload=cfg['workload'], n_cheb=cfg['n_cheb'], cheb_deg=cfg['cheb_deg'], dt=cfg['dt'],
+                            samples_per_step=ns * world, l2='inputs larger than L2 (about 5 GB live per batch)',
+                            precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world),
+                e2e=e2e, gpu_launches=int(launches), roofline=rl, cpu_baseline=cpu,
+                clocks=clk, time_to_0_03eV=tt,
+                setup=dict(seconds=round(t_setup, 2), e_homo=ks['e_homo'], e_lumo=ks['e_lumo'],
+                           gap_eV=round((ks['e_lumo'] - ks['e_homo']) * HA_EV, 4), emin=ks['emin'], emax=ks['emax'],
+                           eig_residual=ks['eig_residual']))
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=5)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--config', default='si35h36_64', choices=sorted(CONFIGS))
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    args = ap.parse_args()
+    cfg = CONFIGS[args.config]
+    if args.impl == 'reference':
+        run_reference(args, cfg)
+    else:
+        run_ours(args, cfg)
+
+
+if __name__ == '__main__':
+    main()

@@ -245,6 +245,38 @@ sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_
                          double vxc, double window, double step, int fp64,
                          double* result_host);
 
+/*
+ * Instrumentation (no counterpart in the paper beyond its per-portion wall times, Table 4).
+ * Kernel kinds for sgw_profile_read:                                                      */
+enum {
+    SGW_PROF_PLANE_STEP = 0,   /* fused xy-plane pass of a Chebyshev term (inverse FFT, V psi,
+                                  KB apply, recurrence, forward FFT)                       */
+    SGW_PROF_PENCIL = 1,       /* z-pencil pass (FFT along z, kinetic multiply, inverse)   */
+    SGW_PROF_KB = 2,           /* KB projector contraction                                 */
+    SGW_PROF_PLANE_FWD = 3,    /* forward xy-plane pass                                    */
+    SGW_PROF_TDH_DENSITY = 4,  /* TDH density + forward xy pass of the Poisson solve       */
+    SGW_PROF_SIGMA = 5,        /* Sigma(t) reduction                                       */
+    SGW_PROF_TIME_ORDER = 6,   /* time ordering                                            */
+    SGW_PROF_OTHER = 7,        /* everything else                                          */
+    SGW_PROF_KINDS = 8
+};
+
+/* enable != 0: from now on record CUDA events on the context's stream around every kernel
+ * launch; resets the accumulated times.  Synchronises. */
+sgw_status sgw_profile(sgw_ctx* ctx, int enable);
+
+/* Accumulated device time (ms, from the recorded events), launch count and algorithmic
+ * (compulsory) HBM bytes of one kernel kind since sgw_profile(ctx, 1): for a plane pass
+ * 8 bytes per vector-point for each complex array it must read or write, 4 per point for
+ * each potential row; for a pencil pass 16 per vector-point; for the KB contraction 8 per
+ * support point and vector plus the projector table.  alg_bytes_host may be NULL.
+ * Synchronises. */
+sgw_status sgw_profile_read(sgw_ctx* ctx, int kind, double* total_ms_host, int64_t* count_host,
+                            double* alg_bytes_host);
+
+/* Number of kernels this context has launched since it was created. */
+sgw_status sgw_launch_count(sgw_ctx* ctx, int64_t* count_host);
+
 #ifdef __cplusplus
 }
 #endif

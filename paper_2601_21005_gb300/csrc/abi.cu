@@ -42,10 +42,71 @@ struct sgw_ctx {
     float2* twM = nullptr;
     int twM_n = 0;
     std::vector<sgw::VecInfo> info_host;
+    // instrumentation: launch counter and CUDA-event timing per kernel kind
+    int64_t launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[SGW_PROF_KINDS];
+    double prof_ms[SGW_PROF_KINDS] = {0};
+    int64_t prof_n[SGW_PROF_KINDS] = {0};
+    double prof_bytes[SGW_PROF_KINDS] = {0};   // algorithmic (compulsory) HBM bytes of the launches
     std::string err;
 };
 
 static std::string g_setup_err;
+
+namespace {
+cudaEvent_t ev_get(sgw_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+// Bracket one kernel launch: counts it and, when profiling, records events around it on the
+// context's stream.
+struct Launch {
+    sgw_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    Launch(sgw_ctx* ctx_, int kind_, int n_kernels = 1, double bytes = 0.0) : c(ctx_), kind(kind_) {
+        c->launches += n_kernels;
+        if (c->prof) {
+            c->prof_bytes[kind] += bytes;
+            a = ev_get(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~Launch() {
+        if (a) {
+            cudaEvent_t b = ev_get(c);
+            cudaEventRecord(b, c->stream);
+            c->ev_pending[kind].push_back({a, b});
+        }
+    }
+};
+// Resolve pending event pairs into accumulated milliseconds (synchronises the stream).
+void prof_flush(sgw_ctx* c) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (int k = 0; k < SGW_PROF_KINDS; ++k) {
+        for (auto& pr : c->ev_pending[k]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) {
+                c->prof_ms[k] += ms;
+                c->prof_n[k] += 1;
+            }
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+        c->ev_pending[k].clear();
+    }
+    cudaGetLastError();
+}
+}  // namespace
 
 namespace {
 
@@ -188,7 +249,8 @@ std::vector<Step> clenshaw_plan(const std::vector<cd>* c, const cd* phase, int K
 // W must hold the forward xy transform of psi_in on entry when w_ready; on exit it holds the
 // transform of the output when want_wout.
 sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2* psi_in, float2* out, int batch,
-                      const float* vpot, const float* dvpot, const sgw::VecInfo* info, bool w_ready, bool want_wout) {
+                      const float* vpot, const float* dvpot, const sgw::VecInfo* info, bool w_ready, bool want_wout,
+                      int vrows = 1) {
     cudaStream_t st = ctx->stream;
     const int n = ctx->n;
     const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
@@ -198,6 +260,7 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
         return SGW_OK;
     }
     if (!w_ready) {
+        Launch L(ctx, SGW_PROF_PLANE_FWD, 1, 16.0 * (double)ctx->ng * batch);
         sgw::launch_plane_fwd(n, psi_in, ctx->W, batch, ctx->tw, st);
         CKL();
     }
@@ -208,11 +271,16 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
         const Step& s = plan[i];
         const float2* b1 = buf(s.b1);
         if (ctx->kb.n_atoms > 0) {
+            // gathered psi (8 B) per support point and vector, plus the support index and beta (20 B)
+            Launch L(ctx, SGW_PROF_KB, 1, (double)ctx->kb.n_sup * (8.0 * batch + 20.0));
             sgw::launch_kb_project(n, ctx->kb, b1, batch, (float)ctx->dV, ctx->kbc, st);
             CKL();
         }
-        sgw::launch_pencil(n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, st);
-        CKL();
+        {
+            Launch L(ctx, SGW_PROF_PENCIL, 1, 16.0 * (double)ctx->ng * batch);
+            sgw::launch_pencil(n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, st);
+            CKL();
+        }
         sgw::StepArgs a{};
         a.W = ctx->W;
         const bool last = (i + 1 == plan.size());
@@ -236,8 +304,16 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
             a.coef.ch[q] = f2(s.ch[q]);
             a.coef.c2[q] = f2(s.c2[q]);
         }
-        sgw::launch_plane_step(n, a, batch, ctx->tw, st);
-        CKL();
+        {
+            // per vector-point: W, b1 in; psi, b2 in when used; out and Wout written; plus the
+            // potential rows (and tangent rows) shared by the vectors, and the KB point index.
+            const double per = 8.0 * (2 + (a.psi ? 1 : 0) + (a.b2 ? 1 : 0) + 1 + (a.Wout ? 1 : 0));
+            double bytes = per * (double)ctx->ng * batch + 4.0 * (double)ctx->ng * vrows * (dvpot ? 2 : 1);
+            if (a.kbc) bytes += 4.0 * (double)ctx->ng + 20.0 * (double)ctx->kb.n_sup;
+            Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
+            sgw::launch_plane_step(n, a, batch, ctx->tw, st);
+            CKL();
+        }
     }
     return SGW_OK;
 }
@@ -345,6 +421,12 @@ void sgw_destroy(sgw_ctx* ctx) {
         if (p) cudaFree(p);
     for (int i = 0; i < 8; ++i)
         if (ctx->work[i]) cudaFree(ctx->work[i]);
+    for (int k = 0; k < SGW_PROF_KINDS; ++k)
+        for (auto& pr : ctx->ev_pending[k]) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -442,14 +524,21 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     if ((s = upload_info(ctx, info))) return s;
     const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
     const float2* in = (const float2*)in_dev;
-    sgw::launch_plane_fwd(ctx->n, in, ctx->W, batch, ctx->tw, ctx->stream);
-    CKL();
+    {
+        Launch L(ctx, SGW_PROF_PLANE_FWD);
+        sgw::launch_plane_fwd(ctx->n, in, ctx->W, batch, ctx->tw, ctx->stream);
+        CKL();
+    }
     if (ctx->kb.n_atoms > 0) {
+        Launch L(ctx, SGW_PROF_KB);
         sgw::launch_kb_project(ctx->n, ctx->kb, in, batch, (float)ctx->dV, ctx->kbc, ctx->stream);
         CKL();
     }
-    sgw::launch_pencil(ctx->n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, ctx->stream);
-    CKL();
+    {
+        Launch L(ctx, SGW_PROF_PENCIL);
+        sgw::launch_pencil(ctx->n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, ctx->stream);
+        CKL();
+    }
     sgw::StepArgs a{};
     a.W = ctx->W;
     a.Wout = nullptr;
@@ -469,8 +558,11 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
         a.coef.ch[q] = make_float2(1.f, 0.f);
         a.coef.c2[q] = make_float2(0.f, 0.f);
     }
-    sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream);
-    CKL();
+    {
+        Launch L(ctx, SGW_PROF_PLANE_STEP);
+        sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream);
+        CKL();
+    }
     return SGW_OK;
 }
 
@@ -505,6 +597,7 @@ sgw_status sgw_spectral_bounds(sgw_ctx* ctx, int n_iter, uint64_t seed, double m
         }
         for (int it = 0; it < n_iter; ++it) {
             if ((s = sgw_apply_h(ctx, v, w, 1))) return s;
+            Launch L(ctx, SGW_PROF_OTHER, 3);   // memset + two kernels
             sgw::launch_dot2((int)ctx->ng, v, w, ctx->scal, st);
             CKL();
             sgw::launch_power_update((int)ctx->ng, w, v, ctx->scal, est + pass, pass == 1 ? est : nullptr,
@@ -654,6 +747,7 @@ sgw_status sgw_white_noise(sgw_ctx* ctx, uint64_t seed, uint32_t stream_id, int 
     if (s) return s;
     if (n_samples < 0 || n_vec < 0 || sample0 < 0 || (!out_dev && n_samples * n_vec > 0))
         return fail(ctx, SGW_EINVAL, "bad noise arguments");
+    Launch L(ctx, SGW_PROF_OTHER);
     sgw::launch_noise((int)ctx->ng, seed, stream_id, sample0, n_samples, n_vec, (float)(1.0 / std::sqrt(ctx->dV)),
                       (float2*)out_dev, ctx->stream);
     CKL();
@@ -668,6 +762,7 @@ sgw_status sgw_prepare_sample(sgw_ctx* ctx, const void* noise_dev, const void* f
     if (n_samples == 0) return SGW_OK;
     if (!noise_dev || !filt_dev || !phi_dev || !eta_dev || !zeta_dev || !source_dev)
         return fail(ctx, SGW_EINVAL, "null prepare pointers");
+    Launch L(ctx, SGW_PROF_OTHER);
     sgw::launch_prepare((int)ctx->ng, (const float2*)noise_dev, (const float2*)filt_dev, phi_dev, n_samples, n_eta,
                         (float2*)eta_dev, (float2*)zeta_dev, source_dev, ctx->stream);
     CKL();
@@ -726,15 +821,16 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
     float* rho0 = dv + ng * n_samples;
     float* vp = rho0 + ng * n_samples;
     // v_p = v_C * source (Poisson, periodic, k = 0 dropped)
-    sgw::launch_real_to_c64(ng * n_samples, source_dev, ctx->B1, st);
-    CKL();
-    sgw::launch_plane_fwd(n, ctx->B1, Wp, n_samples, ctx->tw, st);
-    sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
-    sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 2, nullptr, nullptr, nullptr, nullptr, nullptr, 0, vp, st);
-    CKL();
-    // eta pairs: (eta, d eta = -i v_p eta)
-    sgw::launch_kick((int)ng, (const float2*)eta_dev, vp, n_samples, n_eta, psi, st);
-    CKL();
+    {
+        Launch L(ctx, SGW_PROF_OTHER, 5);
+        sgw::launch_real_to_c64(ng * n_samples, source_dev, ctx->B1, st);
+        sgw::launch_plane_fwd(n, ctx->B1, Wp, n_samples, ctx->tw, st);
+        sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+        sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 2, nullptr, nullptr, nullptr, nullptr, nullptr, 0, vp, st);
+        // eta pairs: (eta, d eta = -i v_p eta)
+        sgw::launch_kick((int)ng, (const float2*)eta_dev, vp, n_samples, n_eta, psi, st);
+        CKL();
+    }
     std::vector<sgw::VecInfo> info(B);
     for (int sm = 0; sm < n_samples; ++sm)
         for (int l = 0; l < 2 * n_eta; ++l) {
@@ -750,13 +846,22 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
     const int64_t uR_stride = (int64_t)(n_steps + 1) * ng;
     for (int j = 0; j <= n_steps; ++j) {
         // H(t_j): density, Poisson of (rho - rho0) + i d rho, potentials and u^R(t_j)
-        sgw::launch_density_fwd(n, psi, n_samples, n_eta, w, rho0, j == 0 ? 1 : 0, Wp, ctx->tw, st);
-        sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
-        sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 1, nullptr, ctx->vloc, vtot, dv, uR_dev + (int64_t)j * ng,
-                              uR_stride, nullptr, st);
+        {
+            Launch L(ctx, SGW_PROF_TDH_DENSITY, 1, (double)ctx->ng * (8.0 * 2 * n_eta * n_samples + 12.0 * n_samples));
+            sgw::launch_density_fwd(n, psi, n_samples, n_eta, w, rho0, j == 0 ? 1 : 0, Wp, ctx->tw, st);
+        }
+        {
+            Launch L(ctx, SGW_PROF_OTHER);
+            sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+        }
+        {
+            Launch L(ctx, SGW_PROF_OTHER);
+            sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 1, nullptr, ctx->vloc, vtot, dv,
+                                  uR_dev + (int64_t)j * ng, uR_stride, nullptr, st);
+        }
         CKL();
         if (j == n_steps) break;
-        if ((s = run_series(ctx, plan, psi, psi, B, vtot, dv, ctx->info, j > 0, true))) return s;
+        if ((s = run_series(ctx, plan, psi, psi, B, vtot, dv, ctx->info, j > 0, true, n_samples))) return s;
     }
     return SGW_OK;
 }
@@ -779,8 +884,11 @@ sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_
         CK(cudaMemcpy(ctx->twM, t.data(), sizeof(float2) * M, cudaMemcpyHostToDevice));
         ctx->twM_n = M;
     }
-    sgw::launch_time_order((int)ctx->ng, uR_dev, (float2*)u_dev, n_samples, n_steps, M, ctx->twM, ctx->stream);
-    CKL();
+    {
+        Launch L(ctx, SGW_PROF_TIME_ORDER, 1, (double)ctx->ng * n_samples * (n_steps + 1) * 12.0);
+        sgw::launch_time_order((int)ctx->ng, uR_dev, (float2*)u_dev, n_samples, n_steps, M, ctx->twM, ctx->stream);
+        CKL();
+    }
     return SGW_OK;
 }
 
@@ -813,14 +921,20 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
     float2* z = (float2*)zeta_dev;
     const int64_t u_ss = (int64_t)(n_steps + 1) * ng;
     for (int j = 0; j <= n_steps; ++j) {
-        sgw::launch_sigma_accum((int)ng, z, phi_dev, (const float2*)u_dev, n_samples, u_ss, j, n_steps, (float)ctx->dV,
-                                fp64_accum, partial, nblk, st);
-        CKL();
+        {
+            Launch L(ctx, SGW_PROF_SIGMA, 1, (double)ng * n_samples * (8.0 * 3 + 4.0));
+            sgw::launch_sigma_accum((int)ng, z, phi_dev, (const float2*)u_dev, n_samples, u_ss, j, n_steps,
+                                    (float)ctx->dV, fp64_accum, partial, nblk, st);
+            CKL();
+        }
         if (j == n_steps) break;
         if ((s = run_series(ctx, plan, z, z, B, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps))) return s;
     }
-    sgw::launch_sigma_reduce(partial, n_samples, n_steps, nblk, ctx->dV, fp64_accum, sigma_dev, st);
-    CKL();
+    {
+        Launch L(ctx, SGW_PROF_OTHER);
+        sgw::launch_sigma_reduce(partial, n_samples, n_steps, nblk, ctx->dV, fp64_accum, sigma_dev, st);
+        CKL();
+    }
     return SGW_OK;
 }
 
@@ -839,6 +953,7 @@ sgw_status sgw_exchange(sgw_ctx* ctx, const void* eta_dev, const float* phi_dev,
     for (int s0 = 0; s0 < n_samples; s0 += per_call) {
         const int ns = std::min(per_call, n_samples - s0);
         const int B = ns * n_eta;
+        Launch L(ctx, SGW_PROF_OTHER, 3);
         sgw::launch_scale_mul((int64_t)B * ng, phi_dev, (int)ng, (const float2*)eta_dev + (size_t)s0 * n_eta * ng,
                               ctx->B1, st);
         sgw::launch_plane_fwd(ctx->n, ctx->B1, ctx->W, B, ctx->tw, st);
@@ -874,12 +989,47 @@ sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_
     if ((s = work(ctx, 5, bytes, &p))) return s;
     double* scan = (double*)p;
     double* result = ctx->scal + 16;
-    sgw::launch_qp(sigma_dev, x_dev, n_samples, n_steps, dt, gamma, eps_ks, vxc, window, step, fp64, scan, n_scan,
-                   result, ctx->stream);
-    CKL();
+    {
+        Launch L(ctx, SGW_PROF_OTHER, 3);
+        sgw::launch_qp(sigma_dev, x_dev, n_samples, n_steps, dt, gamma, eps_ks, vxc, window, step, fp64, scan, n_scan,
+                       result, ctx->stream);
+        CKL();
+    }
     CK(cudaMemcpyAsync(result_host, result, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (std::isnan(result_host[0])) return fail(ctx, SGW_ENOCONV, "no sign change of the QP equation in the window");
+    return SGW_OK;
+}
+
+sgw_status sgw_profile(sgw_ctx* ctx, int enable) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    prof_flush(ctx);
+    for (int k = 0; k < SGW_PROF_KINDS; ++k) {
+        ctx->prof_ms[k] = 0;
+        ctx->prof_n[k] = 0;
+        ctx->prof_bytes[k] = 0;
+    }
+    ctx->prof = enable != 0;
+    return SGW_OK;
+}
+
+sgw_status sgw_profile_read(sgw_ctx* ctx, int kind, double* total_ms_host, int64_t* count_host,
+                            double* alg_bytes_host) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (kind < 0 || kind >= SGW_PROF_KINDS || !total_ms_host || !count_host)
+        return fail(ctx, SGW_EINVAL, "bad profile kind");
+    prof_flush(ctx);
+    *total_ms_host = ctx->prof_ms[kind];
+    *count_host = ctx->prof_n[kind];
+    if (alg_bytes_host) *alg_bytes_host = ctx->prof_bytes[kind];
+    return SGW_OK;
+}
+
+sgw_status sgw_launch_count(sgw_ctx* ctx, int64_t* count_host) {
+    if (!ctx || !count_host) return fail(ctx, SGW_EINVAL, "null argument");
+    *count_host = ctx->launches;
     return SGW_OK;
 }
 

@@ -14,6 +14,8 @@ from . import build as _build
 
 _lib = None
 
+PROF_KINDS = ['plane_step', 'pencil', 'kb_project', 'plane_fwd', 'tdh_density', 'sigma', 'time_order', 'other']
+
 SGW_STATUS = {0: 'SGW_OK', 1: 'SGW_EINVAL', 2: 'SGW_ENOMEM', 3: 'SGW_ECUDA', 4: 'SGW_ESTATE',
               5: 'SGW_ETIMEOUT', 6: 'SGW_ENOCONV'}
 
@@ -47,6 +49,9 @@ _SIGS = {
     'sgw_sigma_c': ([_P, _P, _P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_exchange': ([_P, _P, _P, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_sigma_omega': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _P, _c.c_int, _c.c_int, _P], _c.c_int),
+    'sgw_profile': ([_P, _c.c_int], _c.c_int),
+    'sgw_profile_read': ([_P, _c.c_int, _P, _P, _P], _c.c_int),
+    'sgw_launch_count': ([_P, _P], _c.c_int),
     'sgw_qp_energy': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double, _c.c_double,
                        _c.c_double, _c.c_double, _c.c_int, _P], _c.c_int),
 }
@@ -252,3 +257,19 @@ class Context:
                                                      n_samples, n_steps, dt, gamma, eps_ks, vxc, window, step, fp64,
                                                      r.ctypes.data_as(_P)))
         return dict(eps_qp=r[0], se=r[1], re_sigma=r[2], z=r[3])
+
+    def profile(self, enable):
+        self._ck('sgw_profile', lib().sgw_profile(self._p, 1 if enable else 0))
+
+    def profile_read(self):
+        out = {}
+        for k, name in enumerate(PROF_KINDS):
+            ms, n, by = _c.c_double(), _c.c_int64(), _c.c_double()
+            self._ck('sgw_profile_read', lib().sgw_profile_read(self._p, k, _c.byref(ms), _c.byref(n), _c.byref(by)))
+            out[name] = dict(ms=ms.value, launches=n.value, alg_bytes=by.value)
+        return out
+
+    def launch_count(self):
+        n = _c.c_int64()
+        self._ck('sgw_launch_count', lib().sgw_launch_count(self._p, _c.byref(n)))
+        return n.value
