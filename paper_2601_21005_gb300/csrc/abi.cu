@@ -34,6 +34,7 @@ struct sgw_ctx {
     float2* B2 = nullptr;      // [max_batch][ng]
     sgw::VecInfo* info = nullptr;  // [max_batch]
     float2* kbc = nullptr;     // [max_batch][n_proj]
+    float2* kbp = nullptr;     // [max_batch][total_slots][4] per-plane partial projections
     sgw::KBDev kb;
     double* scal = nullptr;    // small FP64 scratch
     // lazily grown work areas
@@ -271,9 +272,15 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
         const Step& s = plan[i];
         const float2* b1 = buf(s.b1);
         if (ctx->kb.n_atoms > 0) {
-            // gathered psi (8 B) per support point and vector, plus the support index and beta (20 B)
-            Launch L(ctx, SGW_PROF_KB, 1, (double)ctx->kb.n_sup * (8.0 * batch + 20.0));
-            sgw::launch_kb_project(n, ctx->kb, b1, batch, (float)ctx->dV, ctx->kbc, st);
+            if (i == 0 && !w_ready) {
+                // gathered psi (8 B) per support point and vector, plus the support index and beta (20 B)
+                Launch L(ctx, SGW_PROF_KB, 1, (double)ctx->kb.n_sup * (8.0 * batch + 20.0));
+                sgw::launch_kb_project(n, ctx->kb, b1, batch, (float)ctx->dV, ctx->kbc, st);
+            } else {
+                // the previous plane pass left per-plane partial projections of b1
+                Launch L(ctx, SGW_PROF_KB, 1, 32.0 * (double)ctx->kb.total_slots * batch);
+                sgw::launch_kb_reduce(ctx->kb, ctx->kbp, batch, (float)ctx->dV, ctx->kbc, st);
+            }
             CKL();
         }
         {
@@ -296,6 +303,13 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
         a.pt_ptr = ctx->kb.pt_ptr;
         a.pt_atom = ctx->kb.pt_atom;
         a.pt_beta = ctx->kb.pt_beta;
+        a.kbp = (ctx->kb.n_atoms > 0 && a.Wout != nullptr) ? ctx->kbp : nullptr;
+        a.sup_idx = ctx->kb.sup_idx;
+        a.sup_beta = ctx->kb.sup_beta;
+        a.slot_beg = ctx->kb.slot_beg;
+        a.slot_end = ctx->kb.slot_end;
+        a.plane_off = ctx->kb.plane_off;
+        a.total_slots = ctx->kb.total_slots;
         a.n_proj = ctx->kb.n_proj;
         a.ebar = (float)ebar;
         a.alpha = (float)(2.0 / de);
@@ -416,7 +430,8 @@ void sgw_destroy(sgw_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     void* ptrs[] = {ctx->tw, ctx->vloc, ctx->W, ctx->B1, ctx->B2, ctx->info, ctx->kbc, ctx->scal, ctx->twM,
                     ctx->kb.atom_nproj, ctx->kb.atom_off, ctx->kb.sup_idx, ctx->kb.sup_beta, ctx->kb.atom_e,
-                    ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta};
+                    ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta, ctx->kb.slot_beg, ctx->kb.slot_end, ctx->kb.plane_off,
+                    ctx->kb.atom_pos_off, ctx->kb.atom_pos, ctx->kbp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 8; ++i)
@@ -447,11 +462,13 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
     // drop any previous KB data
     CK(cudaStreamSynchronize(ctx->stream));
     void* old[] = {ctx->kb.atom_nproj, ctx->kb.atom_off, ctx->kb.sup_idx, ctx->kb.sup_beta, ctx->kb.atom_e,
-                   ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta, ctx->kbc};
+                   ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta, ctx->kbc, ctx->kb.slot_beg, ctx->kb.slot_end, ctx->kb.plane_off,
+                   ctx->kb.atom_pos_off, ctx->kb.atom_pos, ctx->kbp};
     for (void* p : old)
         if (p) cudaFree(p);
     ctx->kb = sgw::KBDev();
     ctx->kbc = nullptr;
+    ctx->kbp = nullptr;
     if (n_atoms > 0) {
         if (!nproj_host || !sup_off_host || !sup_idx_host || !beta_host || !e_host)
             return fail(ctx, SGW_EINVAL, "KB arrays must be non-null when n_atoms > 0");
@@ -484,7 +501,54 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
                 pt_beta[p] = b;
             }
         }
+        // per-plane slots: one per (plane, atom) pair where the atom's support meets the plane
+        const int n = ctx->n;
+        const int64_t plane_sz = (int64_t)n * n;
+        std::vector<std::vector<int>> plane_atoms(n);
+        for (int a = 0; a < n_atoms; ++a) {
+            std::vector<char> hit(n, 0);
+            for (int64_t i = sup_off_host[a]; i < sup_off_host[a + 1]; ++i) hit[sup_idx_host[i] / plane_sz] = 1;
+            for (int z = 0; z < n; ++z)
+                if (hit[z]) plane_atoms[z].push_back(a);
+        }
+        std::vector<int> plane_off(n + 1, 0);
+        int max_slots = 0;
+        for (int z = 0; z < n; ++z) {
+            plane_off[z + 1] = plane_off[z] + (int)plane_atoms[z].size();
+            max_slots = std::max(max_slots, (int)plane_atoms[z].size());
+        }
+        const int total_slots = plane_off[n];
+        std::vector<std::vector<int>> atom_slots(n_atoms);
+        std::vector<std::vector<int>> slot_of(n);   // slot_of[z][k] = atom of local slot k
+        for (int z = 0; z < n; ++z)
+            for (int k = 0; k < (int)plane_atoms[z].size(); ++k) atom_slots[plane_atoms[z][k]].push_back(plane_off[z] + k);
+        std::vector<int> atom_pos_off(n_atoms + 1, 0), atom_pos;
+        for (int a = 0; a < n_atoms; ++a) {
+            atom_pos_off[a + 1] = atom_pos_off[a] + (int)atom_slots[a].size();
+            atom_pos.insert(atom_pos.end(), atom_slots[a].begin(), atom_slots[a].end());
+        }
+        // support range of each slot: atom a's entries in plane z are contiguous (sorted support)
+        std::vector<int> slot_beg(std::max(total_slots, 1)), slot_end(std::max(total_slots, 1));
+        for (int a = 0; a < n_atoms; ++a) {
+            for (int64_t i = sup_off_host[a]; i < sup_off_host[a + 1]; ++i) {
+                if (i > sup_off_host[a] && sup_idx_host[i] <= sup_idx_host[i - 1])
+                    return fail(ctx, SGW_EINVAL, "each atom's support indices must be strictly increasing");
+            }
+            int q = atom_pos_off[a];
+            int64_t i = sup_off_host[a];
+            while (i < sup_off_host[a + 1]) {
+                const int z = (int)(sup_idx_host[i] / plane_sz);
+                int64_t j = i;
+                while (j < sup_off_host[a + 1] && sup_idx_host[j] / plane_sz == z) ++j;
+                slot_beg[atom_pos[q]] = (int)i;
+                slot_end[atom_pos[q]] = (int)j;
+                ++q;
+                i = j;
+            }
+        }
         sgw::KBDev& kb = ctx->kb;
+        kb.total_slots = total_slots;
+        kb.max_plane_slots = max_slots;
         kb.n_atoms = n_atoms;
         kb.n_proj = 4 * n_atoms;
         kb.n_sup = nsup;
@@ -509,6 +573,22 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
         CK(cudaMemcpy(kb.pt_ptr, cnt.data(), sizeof(int) * (ctx->ng + 1), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.pt_atom, pt_atom.data(), sizeof(int) * nsup, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.pt_beta, pt_beta.data(), sizeof(float4) * nsup, cudaMemcpyHostToDevice));
+        ok = cudaMalloc(&kb.slot_beg, sizeof(int) * std::max(total_slots, 1)) == cudaSuccess &&
+             cudaMalloc(&kb.slot_end, sizeof(int) * std::max(total_slots, 1)) == cudaSuccess &&
+             cudaMalloc(&kb.plane_off, sizeof(int) * (n + 1)) == cudaSuccess &&
+             cudaMalloc(&kb.atom_pos_off, sizeof(int) * (n_atoms + 1)) == cudaSuccess &&
+             cudaMalloc(&kb.atom_pos, sizeof(int) * std::max(total_slots, 1)) == cudaSuccess &&
+             cudaMalloc(&ctx->kbp, sizeof(float2) * 4 * (size_t)std::max(total_slots, 1) * ctx->max_batch) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            return fail(ctx, SGW_ENOMEM, "KB device allocation failed");
+        }
+        CK(cudaMemcpy(kb.slot_beg, slot_beg.data(), sizeof(int) * std::max(total_slots, 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.slot_end, slot_end.data(), sizeof(int) * std::max(total_slots, 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.plane_off, plane_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.atom_pos_off, atom_pos_off.data(), sizeof(int) * (n_atoms + 1), cudaMemcpyHostToDevice));
+        if (total_slots > 0)
+            CK(cudaMemcpy(kb.atom_pos, atom_pos.data(), sizeof(int) * total_slots, cudaMemcpyHostToDevice));
     }
     ctx->have_potential = true;
     return SGW_OK;

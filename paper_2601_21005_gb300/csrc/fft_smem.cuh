@@ -136,4 +136,73 @@ __device__ __forceinline__ void fft_lines(float2* s, const float2* __restrict__ 
     fft_rec<N, 1, NL, LS, ES, NT, DIR>(s, tw);
 }
 
+// ---------------------------------------------------------------- register-ended stages
+// The first Stockham stage (NS = 1) of butterfly j reads elements j + r N/R, and the last
+// stage (NS = N/R) of butterfly j writes elements j + q N/R.  So the inputs of the first stage
+// can be loaded straight from global memory into registers, the outputs of the last stage can
+// be stored straight from registers, and a forward transform whose last radix equals the first
+// radix of the inverse (reversed plan) can hand its outputs to the inverse in registers.
+// Butterfly b = threadIdx.x + p NT of a stage maps to line l = b % NL, index j = b / NL.
+
+// Stage with inputs in registers v[p][r] (= x[l][j + r N/R] before twiddles), outputs to smem.
+template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR, int PER>
+__device__ __forceinline__ void stage_r2s(float2 (&v)[PER][R], float2* s, const float2* __restrict__ tw) {
+    constexpr int NB = N / R;
+    constexpr int TOT = NL * NB;
+    constexpr int TWS = N / (NS * R);
+    static_assert(PER * NT >= TOT, "register array too small");
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * NT;
+        if (TOT % NT == 0 || b < TOT) {
+            const int l = b % NL, j = b / NL;
+            const int k = j % NS;
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[(r * k * TWS) & (N - 1)]);
+                    if (DIR > 0) w.y = -w.y;
+                    v[p][r] = cmul(v[p][r], w);
+                }
+            }
+            Dft<R, DIR>::run(v[p]);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int q = 0; q < R; ++q) s[l * LS + (base + q * NS) * ES] = v[p][q];
+        }
+    }
+    __syncthreads();
+}
+
+// Last stage (NS * R == N) with inputs from smem and outputs kept in registers:
+// v[p][q] = y[l][j + q NS].  Ends with a barrier so that smem may be overwritten.
+template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR, int PER>
+__device__ __forceinline__ void stage_s2r(const float2* s, float2 (&v)[PER][R], const float2* __restrict__ tw) {
+    constexpr int NB = N / R;
+    constexpr int TOT = NL * NB;
+    constexpr int TWS = N / (NS * R);
+    static_assert(NS * R == N, "stage_s2r is the last stage");
+    static_assert(PER * NT >= TOT, "register array too small");
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * NT;
+        if (TOT % NT == 0 || b < TOT) {
+            const int l = b % NL, j = b / NL;
+            const int k = j;   // j < NS
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[p][r] = s[l * LS + (j + r * NB) * ES];
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    float2 w = __ldg(&tw[(r * k * TWS) & (N - 1)]);
+                    if (DIR > 0) w.y = -w.y;
+                    v[p][r] = cmul(v[p][r], w);
+                }
+            }
+            Dft<R, DIR>::run(v[p]);
+        }
+    }
+    __syncthreads();
+}
+
 }  // namespace sgw

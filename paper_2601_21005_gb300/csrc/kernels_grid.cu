@@ -19,6 +19,8 @@ template <int N> struct Cfg {
     static constexpr int TX = 16;     // pencil tile width along kx (16 x 8 B = 128 B rows)
     static constexpr int PENCIL_NT = (TX * N / 8) < 64 ? 64 : (TX * N / 8);
     static constexpr size_t PLANE_SMEM = sizeof(float2) * N * (N + 1);
+    // CTAs per SM the plane kernels are compiled for (register budget 65536 / (NT * MINB))
+    static constexpr int PLANE_MINB = N == 128 ? 1 : (N == 64 ? 4 : 6);
     static constexpr size_t PENCIL_SMEM = sizeof(float2) * N * TX;
 };
 
@@ -33,6 +35,7 @@ __device__ __forceinline__ void st4(float2* p, float2 a, float2 b) {
 template <int N, int NT>
 __device__ __forceinline__ void load_plane(float2* sm, const float2* __restrict__ src) {
     constexpr int P = N + 1;
+#pragma unroll 8
     for (int q = threadIdx.x; q < N * N / 2; q += NT) {
         const int y = q / (N / 2), x = 2 * (q % (N / 2));
         const float4 v = ld4(src + y * N + x);
@@ -44,6 +47,7 @@ __device__ __forceinline__ void load_plane(float2* sm, const float2* __restrict_
 template <int N, int NT>
 __device__ __forceinline__ void store_plane(float2* __restrict__ dst, const float2* sm) {
     constexpr int P = N + 1;
+#pragma unroll 8
     for (int q = threadIdx.x; q < N * N / 2; q += NT) {
         const int y = q / (N / 2), x = 2 * (q % (N / 2));
         st4(dst + y * N + x, sm[y * P + x], sm[y * P + x + 1]);
@@ -59,7 +63,7 @@ __device__ __forceinline__ void fft2_plane(float2* sm, const float2* __restrict_
 
 // ------------------------------------------------------------------ forward plane pass
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
 k_plane_fwd(const float2* __restrict__ in, float2* __restrict__ W, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     constexpr int NT = Cfg<N>::PLANE_NT;
@@ -71,41 +75,96 @@ k_plane_fwd(const float2* __restrict__ in, float2* __restrict__ W, const float2*
 }
 
 // ------------------------------------------------------------------ pencil pass
+// Radix plans along z (forward order; the inverse uses the reversed plan so that the
+// forward's last stage, the k-space multiply and the inverse's first stage stay in registers).
+template <int N> struct ZPlan;
+template <> struct ZPlan<16> { static constexpr int R1 = 4, R2 = 4, R3 = 0; };
+template <> struct ZPlan<32> { static constexpr int R1 = 8, R2 = 4, R3 = 0; };
+template <> struct ZPlan<64> { static constexpr int R1 = 8, R2 = 8, R3 = 0; };
+template <> struct ZPlan<128> { static constexpr int R1 = 8, R2 = 4, R3 = 4; };
+
+template <int N, int KIND>
+__device__ __forceinline__ float kspace_factor(int kx, int ky, int kz, float kscale, float ecut) {
+    const int mx = sfreq(kx, N), my = sfreq(ky, N), mz = sfreq(kz, N);
+    const float k2 = kscale * (float)(mx * mx + my * my + mz * mz);
+    float f;
+    if (KIND == 0) {
+        f = 0.5f * k2;
+        if (ecut > 0.f) f = fminf(f, ecut);
+    } else {
+        f = k2 > 0.f ? 12.566370614359172f / k2 : 0.f;   // 4 pi / k^2
+    }
+    return f * (1.0f / ((float)N * N * N));
+}
+
+// Forward z transform of a tile (TX kx-columns at one ky): global -> registers -> ... ->
+// registers holding X[l][kz = j + q NS_last] (butterfly layout of the last stage).
+template <int N, int NT, int PL, int RL>
+__device__ __forceinline__ void pencil_forward(const float2* __restrict__ base, float2* sm, float2 (&c)[PL][RL],
+                                               const float2* __restrict__ tw) {
+    constexpr int TX = Cfg<N>::TX, R1 = ZPlan<N>::R1, R2 = ZPlan<N>::R2, R3 = ZPlan<N>::R3;
+    constexpr int P1 = (TX * (N / R1) + NT - 1) / NT;
+    float2 a[P1][R1];
+#pragma unroll
+    for (int p = 0; p < P1; ++p) {
+        const int bb = threadIdx.x + p * NT;
+        if ((TX * (N / R1)) % NT == 0 || bb < TX * (N / R1)) {
+            const int l = bb % TX, j = bb / TX;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) a[p][r] = __ldg(base + (size_t)(j + r * (N / R1)) * N * N + l);
+        }
+    }
+    stage_r2s<N, R1, 1, TX, 1, TX, NT, -1>(a, sm, tw);
+    if constexpr (R3 == 0) {
+        stage_s2r<N, R2, R1, TX, 1, TX, NT, -1>(sm, c, tw);
+    } else {
+        fft_stage<N, R2, R1, TX, 1, TX, NT, -1>(sm, tw);
+        stage_s2r<N, R3, R1 * R2, TX, 1, TX, NT, -1>(sm, c, tw);
+    }
+}
+
 template <int N, int KIND>
 __global__ void __launch_bounds__(Cfg<N>::PENCIL_NT)
 k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     constexpr int NT = Cfg<N>::PENCIL_NT, TX = Cfg<N>::TX, NXT = N / TX;
+    constexpr int R1 = ZPlan<N>::R1, R2 = ZPlan<N>::R2, R3 = ZPlan<N>::R3;
+    constexpr int RL = R3 == 0 ? R2 : R3;          // last forward radix = first inverse radix
+    constexpr int NBL = N / RL;                    // butterflies per line of that stage
+    constexpr int PL = (TX * NBL + NT - 1) / NT;
     const int xt = blockIdx.x % NXT, ky = blockIdx.x / NXT;
     float2* base = W + (size_t)blockIdx.y * N * N * N + (size_t)ky * N + xt * TX;
-    for (int q = threadIdx.x; q < N * TX / 2; q += NT) {
-        const int z = q / (TX / 2), l = 2 * (q % (TX / 2));
-        const float4 v = ld4(base + (size_t)z * N * N + l);
-        sm[z * TX + l] = make_float2(v.x, v.y);
-        sm[z * TX + l + 1] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
-    fft_lines<N, TX, 1, TX, NT, -1>(sm, tw);
-    const float inv_n3 = 1.0f / ((float)N * N * N);
-    const int my = sfreq(ky, N);
-    for (int q = threadIdx.x; q < N * TX; q += NT) {
-        const int z = q / TX, l = q % TX;
-        const int mx = sfreq(xt * TX + l, N), mz = sfreq(z, N);
-        const float k2 = kscale * (float)(mx * mx + my * my + mz * mz);
-        float f;
-        if (KIND == 0) {
-            f = 0.5f * k2;
-            if (ecut > 0.f) f = fminf(f, ecut);
-        } else {
-            f = k2 > 0.f ? 12.566370614359172f / k2 : 0.f;   // 4 pi / k^2
+    float2 c[PL][RL];
+    pencil_forward<N, NT, PL, RL>(base, sm, c, tw);
+    // k-space multiply on X[l][kz = j + q NBL]
+#pragma unroll
+    for (int p = 0; p < PL; ++p) {
+        const int bb = threadIdx.x + p * NT;
+        if ((TX * NBL) % NT == 0 || bb < TX * NBL) {
+            const int l = bb % TX, j = bb / TX;
+#pragma unroll
+            for (int q = 0; q < RL; ++q)
+                c[p][q] = cscale(c[p][q], kspace_factor<N, KIND>(xt * TX + l, ky, j + q * NBL, kscale, ecut));
         }
-        sm[q] = cscale(sm[q], f * inv_n3);
     }
-    __syncthreads();
-    fft_lines<N, TX, 1, TX, NT, +1>(sm, tw);
-    for (int q = threadIdx.x; q < N * TX / 2; q += NT) {
-        const int z = q / (TX / 2), l = 2 * (q % (TX / 2));
-        st4(base + (size_t)z * N * N + l, sm[z * TX + l], sm[z * TX + l + 1]);
+    // inverse along z with the reversed plan, first stage from registers
+    stage_r2s<N, RL, 1, TX, 1, TX, NT, +1>(c, sm, tw);
+    constexpr int P1 = (TX * (N / R1) + NT - 1) / NT;
+    float2 a[P1][R1];
+    if constexpr (R3 == 0) {
+        stage_s2r<N, R1, N / R1, TX, 1, TX, NT, +1>(sm, a, tw);
+    } else {
+        fft_stage<N, R2, R3, TX, 1, TX, NT, +1>(sm, tw);
+        stage_s2r<N, R1, N / R1, TX, 1, TX, NT, +1>(sm, a, tw);
+    }
+#pragma unroll
+    for (int p = 0; p < P1; ++p) {
+        const int bb = threadIdx.x + p * NT;
+        if ((TX * (N / R1)) % NT == 0 || bb < TX * (N / R1)) {
+            const int l = bb % TX, j = bb / TX;
+#pragma unroll
+            for (int q = 0; q < R1; ++q) base[(size_t)(j + q * (N / R1)) * N * N + l] = a[p][q];
+        }
     }
 }
 
@@ -118,25 +177,28 @@ k_pencil_energy(const float2* __restrict__ W, int per, float kscale, double dvn,
     extern __shared__ float2 sm[];
     __shared__ double red[32];
     constexpr int NT = Cfg<N>::PENCIL_NT, TX = Cfg<N>::TX, NXT = N / TX;
+    constexpr int R2 = ZPlan<N>::R2, R3 = ZPlan<N>::R3;
+    constexpr int RL = R3 == 0 ? R2 : R3;
+    constexpr int NBL = N / RL;
+    constexpr int PL = (TX * NBL + NT - 1) / NT;
     const int xt = blockIdx.x % NXT, ky = blockIdx.x / NXT;
     const float2* base = W + (size_t)blockIdx.y * N * N * N + (size_t)ky * N + xt * TX;
-    for (int q = threadIdx.x; q < N * TX / 2; q += NT) {
-        const int z = q / (TX / 2), l = 2 * (q % (TX / 2));
-        const float4 v = ld4(base + (size_t)z * N * N + l);
-        sm[z * TX + l] = make_float2(v.x, v.y);
-        sm[z * TX + l + 1] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
-    fft_lines<N, TX, 1, TX, NT, -1>(sm, tw);
+    float2 c[PL][RL];
+    pencil_forward<N, NT, PL, RL>(base, sm, c, tw);
     const int my = sfreq(ky, N);
     double s = 0.0;
-    for (int q = threadIdx.x; q < N * TX; q += NT) {
-        const int z = q / TX, l = q % TX;
-        const int mx = sfreq(xt * TX + l, N), mz = sfreq(z, N);
-        const double k2 = (double)kscale * (double)(mx * mx + my * my + mz * mz);
-        if (k2 > 0.0) {
-            const double a = sm[q].x, b = sm[q].y;
-            s += 12.566370614359172 / k2 * (a * a + b * b);
+#pragma unroll
+    for (int p = 0; p < PL; ++p) {
+        const int bb = threadIdx.x + p * NT;
+        if ((TX * NBL) % NT == 0 || bb < TX * NBL) {
+            const int l = bb % TX, j = bb / TX;
+            const int mx = sfreq(xt * TX + l, N);
+#pragma unroll
+            for (int q = 0; q < RL; ++q) {
+                const int mz = sfreq(j + q * NBL, N);
+                const double k2 = (double)kscale * (double)(mx * mx + my * my + mz * mz);
+                if (k2 > 0.0) s += 12.566370614359172 / k2 * ((double)c[p][q].x * c[p][q].x + (double)c[p][q].y * c[p][q].y);
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -151,7 +213,7 @@ k_pencil_energy(const float2* __restrict__ W, int per, float kscale, double dvn,
 
 // ------------------------------------------------------------------ fused Chebyshev step
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
 k_plane_step(StepArgs a, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
@@ -170,6 +232,8 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
     const float2* bp = (dV != nullptr) ? a.b1 + ((size_t)inf.partner * N + z) * N * N : nullptr;
     const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
     const float ebar = a.ebar, alpha = a.alpha;
+    const bool want_kbp = a.kbp != nullptr;
+#pragma unroll 2
     for (int q = threadIdx.x; q < N * N / 2; q += NT) {
         const int y = q / (N / 2), x = 2 * (q % (N / 2));
         const int o = y * N + x;
@@ -223,13 +287,37 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
     }
     if (a.Wout == nullptr) return;
     __syncthreads();
+    if (want_kbp) {
+        // partial projections of `out` on this plane: one warp per (plane, atom) slot sums the
+        // atom's support points in the plane from shared memory, in a fixed order
+        const int s0 = __ldg(a.plane_off + z), s1 = __ldg(a.plane_off + z + 1);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int zo = z * N * N;
+        for (int k = s0 + warp; k < s1; k += NT / 32) {
+            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const int e1 = __ldg(a.slot_end + k);
+            for (int e = __ldg(a.slot_beg + k) + lane; e < e1; e += 32) {
+                const int o = __ldg(a.sup_idx + e) - zo;
+                const float2 v = sm[(o / N) * P + (o % N)];
+                const float4 be = __ldg(a.sup_beta + e);
+                acc[0] += be.x * v.x; acc[1] += be.x * v.y;
+                acc[2] += be.y * v.x; acc[3] += be.y * v.y;
+                acc[4] += be.z * v.x; acc[5] += be.z * v.y;
+                acc[6] += be.w * v.x; acc[7] += be.w * v.y;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
+            if (lane < 8) reinterpret_cast<float*>(a.kbp + ((size_t)b * a.total_slots + k) * 4)[lane] = acc[lane];
+        }
+    }
     fft2_plane<N, NT, -1>(sm, tw);
     store_plane<N, NT>(a.Wout + plane, sm);
 }
 
 // ------------------------------------------------------------------ inverse plane pass
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
 k_plane_inv(const float2* __restrict__ W, const float2* __restrict__ tw, int mode, float2* out_c,
             const float* __restrict__ vloc, float* vtot, float* dv, float* uR, int64_t uR_stride, float* out_re) {
     extern __shared__ float2 sm[];
@@ -261,7 +349,7 @@ k_plane_inv(const float2* __restrict__ W, const float2* __restrict__ tw, int mod
 // ------------------------------------------------------------------ TDH density
 // Sample s owns batch vectors [s*2*n_eta, (s+1)*2*n_eta): eta_l then d eta_l.
 template <int N>
-__global__ void __launch_bounds__(Cfg<N>::PLANE_NT)
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
 k_density_fwd(const float2* __restrict__ psi, int n_eta, float weight, float* rho0, int store_rho0,
               float2* __restrict__ Wp, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
@@ -331,12 +419,45 @@ k_kb_project(const int64_t* __restrict__ atom_off, const int* __restrict__ sup_i
     }
 }
 
+// kbc[b][4a + p] = E_ap dV sum_{slots of a} kbp[b][slot][p]  (fixed order: increasing plane)
+__global__ void k_kb_reduce(const int* __restrict__ atom_pos_off, const int* __restrict__ atom_pos,
+                            const float4* __restrict__ atom_e, const float2* __restrict__ kbp, int n_atoms, int batch,
+                            int total_slots, int n_proj, float dV, float2* __restrict__ kbc) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= batch * n_atoms * 4) return;
+    const int p = t & 3, a = (t >> 2) % n_atoms, b = (t >> 2) / n_atoms;
+    float2 acc = make_float2(0.f, 0.f);
+    const int q1 = __ldg(atom_pos_off + a + 1);
+    for (int q = __ldg(atom_pos_off + a); q < q1; ++q) {
+        const float2 v = __ldg(kbp + ((size_t)b * total_slots + __ldg(atom_pos + q)) * 4 + p);
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    const float4 e = __ldg(atom_e + a);
+    const float ep = (p == 0 ? e.x : (p == 1 ? e.y : (p == 2 ? e.z : e.w))) * dV;
+    kbc[(size_t)b * n_proj + a * 4 + p] = make_float2(ep * acc.x, ep * acc.y);
+}
+
+void launch_kb_reduce(const KBDev& kb, const float2* kbp, int batch, float dV, float2* kbc, cudaStream_t st) {
+    const int total = batch * kb.n_atoms * 4;
+    if (total == 0) return;
+    k_kb_reduce<<<(total + 255) / 256, 256, 0, st>>>(kb.atom_pos_off, kb.atom_pos, kb.atom_e, kbp, kb.n_atoms, batch,
+                                                    kb.total_slots, kb.n_proj, dV, kbc);
+}
+
 // ------------------------------------------------------------------ launchers
 bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
 
 template <int N> static cudaError_t set_attrs() {
     cudaError_t e = cudaSuccess;
     const int ps = (int)Cfg<N>::PLANE_SMEM;
+    const int mx = (int)cudaSharedmemCarveoutMaxShared;
+    if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_step<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_density_fwd<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_pencil<N, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_pencil<N, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     if ((e = cudaFuncSetAttribute(k_plane_step<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     if ((e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;

@@ -34,6 +34,18 @@ struct KBDev {
     int* pt_ptr = nullptr;       // [ng + 1]
     int* pt_atom = nullptr;      // [n_sup]
     float4* pt_beta = nullptr;   // [n_sup]
+    // per-plane partial projections: plane z owns slots plane_off[z] .. plane_off[z+1]-1, one per
+    // atom whose support meets the plane; slot k covers the atom-major support entries
+    // slot_beg[k] .. slot_end[k]-1 (the atom's points in that plane, contiguous because each
+    // atom's support is sorted by grid index); atom a's slots (in increasing z) are
+    // atom_pos[atom_pos_off[a] .. atom_pos_off[a+1]).
+    int total_slots = 0;
+    int max_plane_slots = 0;
+    int* slot_beg = nullptr;     // [total_slots]
+    int* slot_end = nullptr;     // [total_slots]
+    int* plane_off = nullptr;    // [n + 1]
+    int* atom_pos_off = nullptr; // [n_atoms + 1]
+    int* atom_pos = nullptr;     // [total_slots]
 };
 
 struct StepArgs {
@@ -50,6 +62,14 @@ struct StepArgs {
     const int* pt_ptr;
     const int* pt_atom;
     const float4* pt_beta;
+    // partial projections of `out` (nullptr: skip): kbp[b][slot][4] = sum_plane beta_ap(r) out(r)
+    float2* kbp;
+    const int* sup_idx;
+    const float4* sup_beta;
+    const int* slot_beg;
+    const int* slot_end;
+    const int* plane_off;
+    int total_slots;
     int n_proj;
     float ebar, alpha;
     StepCoef coef;
@@ -73,6 +93,8 @@ void launch_plane_inv(int n, const float2* W, int batch, const float2* tw, int m
                       float* out_re, cudaStream_t st);
 void launch_kb_project(int n, const KBDev& kb, const float2* b1, int batch, float dV, float2* kbc,
                        cudaStream_t st);
+// kbc[b][4a + p] = E_ap dV sum over atom a's plane slots of kbp[b][slot][p]
+void launch_kb_reduce(const KBDev& kb, const float2* kbp, int batch, float dV, float2* kbc, cudaStream_t st);
 // density of TDH pairs for each sample, packed as (rho - rho0) + i d rho, fwd xy transformed into Wp.
 void launch_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0,
                         int store_rho0, float2* Wp, const float2* tw, cudaStream_t st);

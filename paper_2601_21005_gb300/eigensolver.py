@@ -5,10 +5,22 @@ items 4-5 of the inputs; Sec. 3).  For the synthetic systems here they come from
 Chebyshev-filtered subspace iteration (Zhou & Saad, 2007): the block is filtered with
 T_m(H~) on the interval [cut, E_max] (which damps everything above `cut` and amplifies
 the states below it), orthonormalised, and rotated by a Rayleigh-Ritz step; `cut` follows
-the largest Ritz value.  The H applications and the filter run in libsgw; the small
-dense linear algebra (QR, m x m eigh) uses torch.linalg.
+the largest Ritz value.  The H applications and the filter run in libsgw; the block
+products run as torch matmuls, and the m x m factorisations (Cholesky, eigh) on the host.
 """
 import numpy as np
+
+
+def _orth_rows(A, torch):
+    """Rows of A orthonormalised by Cholesky QR, done twice, with FP64 Gram matrices."""
+    for _ in range(2):
+        A64 = A.to(torch.complex128)
+        G = (A64.conj() @ A64.transpose(0, 1)).cpu().numpy()      # G_ij = <a_i|a_j>
+        G = 0.5 * (G + G.conj().T)
+        L = np.linalg.cholesky(G.T)                               # G^T = L L^H
+        Li = np.linalg.inv(L)
+        A = (torch.from_numpy(Li).to(A64.device) @ A64).to(torch.complex64)
+    return A.contiguous()
 
 
 def lowest_states(ctx, n_want, emin, emax, extra=24, degree=60, max_iter=40, tol=1e-5, seed=4242):
@@ -25,40 +37,35 @@ def lowest_states(ctx, n_want, emin, emax, extra=24, degree=60, max_iter=40, tol
     coeff[-1] = 1.0
 
     def rayleigh_ritz(Q):
-        # Q: [m, ng] with orthonormal rows (Euclidean)
         ctx.apply_h(Q, Y)
-        Hs = (Q.conj() @ Y.transpose(0, 1)).to(torch.complex128)
+        Q64, Y64 = Q.to(torch.complex128), Y.to(torch.complex128)
+        Hs = (Q64.conj() @ Y64.transpose(0, 1)).cpu().numpy()    # <q_i|H q_j>
         Hs = 0.5 * (Hs + Hs.conj().T)
-        w, V = torch.linalg.eigh(Hs)
-        Vc = V.to(torch.complex64)
-        Qn = (Vc.T @ Q)
-        HQ = (Vc.T @ Y)
-        res = torch.linalg.vector_norm(HQ - w.to(torch.float32)[:, None] * Qn, dim=1)
-        return w.cpu().numpy(), Qn, res.cpu().numpy()
+        w, V = np.linalg.eigh(Hs)
+        R = torch.from_numpy(V.T.copy()).to(Q64.device)        # new q_k = sum_i V_ik q_i
+        Qn = (R @ Q64)
+        HQ = (R @ Y64)
+        res = torch.sqrt(torch.sum(torch.abs(HQ - torch.from_numpy(w).to(Q64.device)[:, None] * Qn) ** 2, dim=1))
+        return w, Qn.to(torch.complex64).contiguous(), res.cpu().numpy()
 
-    def orth(A):
-        q, _ = torch.linalg.qr(A.transpose(0, 1))
-        return q.transpose(0, 1).contiguous()
-
-    Q = orth(X)
+    Q = _orth_rows(X, torch)
     w, Q, res = rayleigh_ritz(Q)
     for _ in range(max_iter):
         if np.max(res[:n_want + 1]) < tol * max(1.0, np.max(np.abs(w[:n_want + 1]))):
             break
         cut = float(w[-1])
         ctx.set_spectrum(cut, emax)
-        ctx.filter_occupied(coeff, Q.contiguous(), X)
-        Q = orth(X)
+        ctx.filter_occupied(coeff, Q, X)
+        Q = _orth_rows(X, torch)
         w, Q, res = rayleigh_ritz(Q)
     ctx.set_spectrum(emin, emax)
     phis = []
-    h3 = ctx.dV
     for i in range(n_want):
         q = Q[i].cpu().numpy().astype(np.complex128)
         k = np.argmax(np.abs(q))
         q = q * np.exp(-1j * np.angle(q[k]))
         r = q.real
-        r /= np.sqrt(h3 * np.sum(r * r))
+        r /= np.sqrt(ctx.dV * np.sum(r * r))
         if r.sum() < 0:
             r = -r
         phis.append(r)

@@ -1,0 +1,50 @@
+"""Micro-benchmark of the propagation kernels on one batch (also the small case for ncu).
+
+    python -m paper_2601_21005_gb300.kernel_bench [--n 64] [--batch 64] [--steps 2] [--deg 16]
+
+Sets up the Si35H36 cluster (local + KB potentials) on an n^3 grid, fills a batch of
+complex vectors with Philox noise and propagates it n_steps steps with the degree-`deg`
+Chebyshev expansion through the C ABI, timing each kernel kind with CUDA events.  Device
+memory: four batch-sized complex arrays (0.5 GB at 64^3 x 64).
+"""
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    import torch
+    from . import build, sgw, synth
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--n', type=int, default=64)
+    ap.add_argument('--batch', type=int, default=64)
+    ap.add_argument('--steps', type=int, default=2)
+    ap.add_argument('--deg', type=int, default=16)
+    ap.add_argument('--no-kb', action='store_true')
+    args = ap.parse_args()
+    build.build()
+    s = synth.si_cluster(n=args.n, h=0.5, radius=10.5 if args.n >= 64 else 4.5)
+    ctx = sgw.Context(args.n, 0.5, max_batch=args.batch)
+    ctx.set_potential(torch.as_tensor(s['vloc'].reshape(-1).astype(np.float32)).cuda(),
+                      [] if args.no_kb else s['kb_atoms'])
+    ctx.set_spectrum(-3.2, 62.2)
+    ng = args.n ** 3
+    psi = torch.empty(args.batch, ng, dtype=torch.complex64, device='cuda')
+    ctx.white_noise(5, 3, 0, 1, args.batch, psi)
+    ctx.propagate(psi, 1, 0.05, args.deg)          # warm-up
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.propagate(psi, args.steps, 0.05, args.deg)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    out = {}
+    for k, v in prof.items():
+        if v['launches']:
+            out[k] = dict(launches=v['launches'], avg_us=round(1e3 * v['ms'] / v['launches'], 2),
+                          alg_GBps=round(v['alg_bytes'] / (v['ms'] * 1e-3) / 1e9, 1) if v['alg_bytes'] else None)
+    print(json.dumps(dict(n=args.n, batch=args.batch, steps=args.steps, deg=args.deg, kernels=out)))
+
+
+if __name__ == '__main__':
+    main()
