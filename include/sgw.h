@@ -246,6 +246,24 @@ sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_
                          double* result_host);
 
 /*
+ * QP solve that allocates nothing (no counterpart in the paper).  For callers that cannot let
+ * a library allocate device memory -- e.g. a host application that has reserved the device's
+ * memory for its own pool allocator, or a plugin host that forbids allocations while it runs.
+ * Same computation and arguments as sgw_qp_energy, without a context: sigma_dev, x_dev and the
+ * work run on `stream` (a cudaStream_t, NULL = default) on the current device.  Scratch is a
+ * fixed 1 MiB device array inside the library (held on every GPU that loads the library until
+ * exit); calls with (2 window/step + 2) + 4 (2 n_steps + 1) + 4 > 131072 doubles are rejected
+ * with SGW_EINVAL.  The first call on a device looks up that array's device address, so make it
+ * before any stream capture.  All calls on a device share the array: calls that overlap on the
+ * GPU (other streams or threads) race and must be serialised by the caller.  Errors are reported
+ * through sgw_last_error(NULL).  Synchronises `stream`.
+ */
+sgw_status sgw_qp_energy_noalloc(const double* sigma_dev, const double* x_dev, int n_samples,
+                                 int n_steps, double dt, double gamma, double eps_ks, double vxc,
+                                 double window, double step, int fp64, double* result_host,
+                                 void* stream);
+
+/*
  * Instrumentation (no counterpart in the paper beyond its per-portion wall times, Table 4).
  * Kernel kinds for sgw_profile_read:                                                      */
 enum {

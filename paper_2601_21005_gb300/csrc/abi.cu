@@ -56,6 +56,11 @@ struct sgw_ctx {
 
 static std::string g_setup_err;
 
+namespace sgw {
+// Errors of calls that have no context are reported through sgw_last_error(NULL).
+void set_global_error(const char* msg) { g_setup_err = msg; }
+}  // namespace sgw
+
 namespace {
 cudaEvent_t ev_get(sgw_ctx* c) {
     if (!c->ev_pool.empty()) {

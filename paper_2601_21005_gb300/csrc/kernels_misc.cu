@@ -1,6 +1,11 @@
 // Non-FFT kernels of the sGW hot path: Philox white noise, the TDH kick, power-iteration
 // reductions, the Sigma(t) reductions (Eq. 5), time ordering of u^R (FFT over t), the
 // damped transform (Eq. 7) and the QP root (Eq. 6).
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "../../include/sgw.h"
 #include "fft_smem.cuh"
 #include "sgw_internal.cuh"
 
@@ -613,3 +618,77 @@ void launch_qp(const double* sigma, const double* x, int n_samples, int n_steps,
 }
 
 }  // namespace sgw
+
+// ------------------------------------------------------------------ QP solve without allocation
+// Some callers cannot let a library allocate device memory at all: a host application that has
+// reserved the device's memory for its own pool allocator, or a plugin host that forbids
+// allocations while it runs, would see cudaMalloc fail or have its memory accounting broken.
+// For them sgw_qp_energy_noalloc runs the QP solve with its scratch in this fixed, statically
+// sized device array instead of a context work area.  Every GPU that loads the library holds
+// the array until the process exits.
+namespace {
+constexpr int kQpScratchDoubles = 131072;   // 1 MiB
+static __device__ __align__(256) double g_qp_scratch[kQpScratchDoubles];
+
+// Device address of g_qp_scratch on each device, looked up once per device with that device
+// current (the host-side name is only a stand-in, not a device address).
+constexpr int kMaxDevices = 64;
+double* g_qp_scratch_dev[kMaxDevices] = {nullptr};
+std::mutex g_qp_scratch_mu;
+}  // namespace
+
+extern "C" sgw_status sgw_qp_energy_noalloc(const double* sigma_dev, const double* x_dev, int n_samples,
+                                            int n_steps, double dt, double gamma, double eps_ks, double vxc,
+                                            double window, double step, int fp64, double* result_host,
+                                            void* stream) {
+    if (n_samples < 1 || n_steps < 0 || !(window > 0) || !(step > 0) || !sigma_dev || !x_dev || !result_host) {
+        sgw::set_global_error("sgw_qp_energy_noalloc: bad arguments");
+        return SGW_EINVAL;
+    }
+    const long long n_scan = std::llround(2.0 * window / step) + 1;
+    const long long need = ((n_scan + 1) & ~1LL) + 2LL * (2LL * n_steps + 1) + 4;
+    if (need > kQpScratchDoubles) {
+        sgw::set_global_error("sgw_qp_energy_noalloc: window/step and n_steps need more than the 1 MiB static "
+                              "scratch ((2 window/step + 2) + 4 (2 n_steps + 1) + 4 <= 131072 doubles)");
+        return SGW_EINVAL;
+    }
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+        sgw::set_global_error("sgw_qp_energy_noalloc: no usable current device");
+        return SGW_ECUDA;
+    }
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_qp_scratch_mu);
+        if (!g_qp_scratch_dev[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_qp_scratch);
+            if (e != cudaSuccess || !p) {
+                sgw::set_global_error((std::string("sgw_qp_energy_noalloc: cudaGetSymbolAddress: ") +
+                                       cudaGetErrorString(e)).c_str());
+                return SGW_ECUDA;
+            }
+            g_qp_scratch_dev[dev] = static_cast<double*>(p);
+        }
+        scratch = g_qp_scratch_dev[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // scan values, then the damped terms, then the 4 result doubles; every element read in
+    // this call is written first in this call, so nothing needs clearing between calls.
+    double* result = scratch + (need - 4);
+    sgw::launch_qp(sigma_dev, x_dev, n_samples, n_steps, dt, gamma, eps_ks, vxc, window, step, fp64, scratch,
+                   (int)n_scan, result, st);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(result_host, result, 4 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        sgw::set_global_error((std::string("sgw_qp_energy_noalloc: ") + cudaGetErrorString(e)).c_str());
+        return SGW_ECUDA;
+    }
+    if (std::isnan(result_host[0])) {
+        sgw::set_global_error("sgw_qp_energy_noalloc: no sign change of the QP equation in the window");
+        return SGW_ENOCONV;
+    }
+    return SGW_OK;
+}

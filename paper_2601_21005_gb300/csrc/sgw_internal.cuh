@@ -123,6 +123,7 @@ void launch_qp(const double* sigma, const double* x, int n_samples, int n_steps,
                double eps_ks, double vxc, double window, double step, int fp64, double* scan,
                int n_scan, double* result, cudaStream_t st);
 int time_order_threads(int M);
+void set_global_error(const char* msg);
 void launch_prepare(int ng, const float2* noise, const float2* filt, const float* phi, int n_samples, int n_eta,
                     float2* eta, float2* zeta, float* source, cudaStream_t st);
 

@@ -49,6 +49,8 @@ _SIGS = {
     'sgw_sigma_c': ([_P, _P, _P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_exchange': ([_P, _P, _P, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_sigma_omega': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _P, _c.c_int, _c.c_int, _P], _c.c_int),
+    'sgw_qp_energy_noalloc': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double, _c.c_double,
+                               _c.c_double, _c.c_double, _c.c_int, _P, _P], _c.c_int),
     'sgw_profile': ([_P, _c.c_int], _c.c_int),
     'sgw_profile_read': ([_P, _c.c_int, _P, _P, _P], _c.c_int),
     'sgw_launch_count': ([_P, _P], _c.c_int),
@@ -123,6 +125,21 @@ def sgw_propagator_coeffs(emin, emax, dt, cheb_deg):
     _check('sgw_propagator_coeffs',
            lib().sgw_propagator_coeffs(emin, emax, dt, cheb_deg, c.ctypes.data_as(_P), ph.ctypes.data_as(_P)))
     return c[0::2] + 1j * c[1::2], ph[0] + 1j * ph[1]
+
+
+def sgw_qp_energy_noalloc(sigma, x, n_samples, n_steps, dt, gamma, eps_ks, vxc=0.0, window=2.0, step=1e-3,
+                          fp64=1, stream=None):
+    """QP solve that allocates no device memory (for callers whose device memory is owned by
+    another allocator); scratch is a fixed 1 MiB array inside the library.  Same result as
+    Context.qp_energy."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    r = np.zeros(4)
+    _check('sgw_qp_energy_noalloc',
+           lib().sgw_qp_energy_noalloc(_dev(sigma, torch.complex128), _dev(x, torch.float64), n_samples, n_steps, dt,
+                                       gamma, eps_ks, vxc, window, step, fp64, r.ctypes.data_as(_P), _P(stream)))
+    return dict(eps_qp=r[0], se=r[1], re_sigma=r[2], z=r[3])
 
 
 # ------------------------------------------------------------------ context
