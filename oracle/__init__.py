@@ -13,6 +13,8 @@ Modules:
   sgw          white noise, filtering, linear-response TDH, time ordering,
                zeta propagation, Sigma(t) (Eq. 4-5), exchange, Sigma(omega) (Eq. 7),
                QP equation (Eq. 6), statistics
+  mlp          control variate: features of zeta-bar, the MLP (forward, backward,
+               Adam) in FP64, and the unbiased paired estimator
 
 Every function is pinned by tests against closed forms, LAPACK eigh / Casida
 dense solves, published known-answer vectors or brute force.

@@ -1,0 +1,131 @@
+"""FP64 oracle: the learned control variate for the stochastic Sigma_c(t).
+
+TEST INFRASTRUCTURE: part of the CPU oracle; only tests, the smoke check and the
+CPU-baseline leg of the benchmark may use it.
+
+The paper has no learned part; this is the control variate the hot path adds around the
+plain sROI estimator (a sample's Sigma_i(t) is a quadratic form in its random vector
+zeta-bar_i, Eq. 4-5, so cheap functions of zeta-bar predict part of it):
+
+* features of a sample: the Fourier coefficients F(k) = sum_r s(r) e^{-i k.r} dV of the
+  source s = zeta-bar * phi on the shells 0 < |m|^2 <= m2max (k = 2 pi m / L, one of each
+  +-k pair, the half space whose first non-zero component of m is positive), each weighted
+  by sqrt(4 pi)/|k| (the Coulomb kernel's square root), as real and imaginary parts; then
+  F(0) = <phi|zeta-bar> (real part);
+* network: layers h_1 = tanh(x W1 + b1), h_2 = tanh(h_1 W2 + b2), h_3 = tanh(h_2 W3 + b3),
+  y = h_3 W4 + b4; loss = mean over samples and outputs of (y - t)^2; Adam;
+* estimator: with M cheap samples (features only) and n paired samples (features and the
+  plain Sigma_i), the rows z_i = mean_j f(x_j) + Y_i - f(x_i) have mean
+  mean_j f(x_j) + mean_i (Y_i - f(x_i)), which is unbiased for E[Y] whatever f is, and
+  their spread gives the standard error; with f = 0 they are the plain samples.
+"""
+import numpy as np
+
+
+def kset(m2max):
+    """Integer wave vectors m, 0 < |m|^2 <= m2max, one of each +-m pair (first non-zero > 0)."""
+    r = int(np.floor(np.sqrt(m2max)))
+    out = []
+    for a in range(-r, r + 1):
+        for b in range(-r, r + 1):
+            for c in range(-r, r + 1):
+                m = (a, b, c)
+                n2 = a * a + b * b + c * c
+                if 0 < n2 <= m2max:
+                    first = next(x for x in m if x != 0)
+                    if first > 0:
+                        out.append(m)
+    return np.array(sorted(out, key=lambda m: (m[0] ** 2 + m[1] ** 2 + m[2] ** 2, m)), dtype=np.int64)
+
+
+def features(zbar, phi, n, h, m2max):
+    """Feature vector of one sample (zbar, phi: [n, n, n] real arrays indexed [z, y, x]).
+
+    m = (mx, my, mz); F(m) = dV sum_r s(r) exp(-2 pi i (mx x + my y + mz z) / n) by FFT.
+    """
+    s = zbar * phi
+    dV = h ** 3
+    L = n * h
+    F = np.fft.fftn(s) * dV            # axes (z, y, x): F[mz, my, mx]
+    ks = kset(m2max)
+    vals = []
+    for mx, my, mz in ks:
+        kk = 2 * np.pi / L * np.sqrt(mx * mx + my * my + mz * mz)
+        vals.append(F[mz % n, my % n, mx % n] * np.sqrt(4 * np.pi) / kk)
+    vals = np.array(vals)
+    return np.concatenate([vals.real, vals.imag, [F[0, 0, 0].real]])
+
+
+def features_direct(zbar, phi, n, h, m2max):
+    """Same features by the plain DFT sum (no FFT), for pinning `features` on tiny grids."""
+    s = zbar * phi
+    dV = h ** 3
+    L = n * h
+    idx = np.arange(n)
+    Z, Y, X = np.meshgrid(idx, idx, idx, indexing='ij')
+    ks = kset(m2max)
+    vals = []
+    for mx, my, mz in ks:
+        ph = np.exp(-2j * np.pi * (mx * X + my * Y + mz * Z) / n)
+        kk = 2 * np.pi / L * np.sqrt(mx * mx + my * my + mz * mz)
+        vals.append(dV * np.sum(s * ph) * np.sqrt(4 * np.pi) / kk)
+    vals = np.array(vals)
+    return np.concatenate([vals.real, vals.imag, [dV * np.sum(s)]])
+
+
+# ---------------------------------------------------------------- network
+def init_params(n_in, width, n_out, seed):
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights, zero biases (numpy generator)."""
+    rng = np.random.default_rng(seed)
+    dims = [n_in, width, width, width, n_out]
+    p = []
+    for i in range(4):
+        a = 1.0 / np.sqrt(dims[i])
+        p.append(rng.uniform(-a, a, size=(dims[i], dims[i + 1])))
+        p.append(np.zeros(dims[i + 1]))
+    return p
+
+
+def forward(p, x):
+    """Returns the output and the cache of pre-activations and activations."""
+    acts = [x]
+    pre = []
+    a = x
+    for i in range(4):
+        z = a @ p[2 * i] + p[2 * i + 1]
+        pre.append(z)
+        a = np.tanh(z) if i < 3 else z
+        acts.append(a)
+    return a, (acts, pre)
+
+
+def loss_and_grads(p, x, t):
+    """Mean-squared loss over all M x n_out entries and its gradients (backpropagation)."""
+    y, (acts, pre) = forward(p, x)
+    M, O = y.shape
+    loss = np.mean((y - t) ** 2)
+    d = 2.0 * (y - t) / (M * O)
+    g = [None] * 8
+    for i in reversed(range(4)):
+        if i < 3:
+            d = d * (1.0 - np.tanh(pre[i]) ** 2)
+        g[2 * i] = acts[i].T @ d
+        g[2 * i + 1] = d.sum(axis=0)
+        d = d @ p[2 * i].T
+    return loss, g
+
+
+def adam_step(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba) in place; `step` counts from 1."""
+    for i in range(len(p)):
+        m[i] = b1 * m[i] + (1 - b1) * g[i]
+        v[i] = b2 * v[i] + (1 - b2) * g[i] ** 2
+        mh = m[i] / (1 - b1 ** step)
+        vh = v[i] / (1 - b2 ** step)
+        p[i] = p[i] - lr * mh / (np.sqrt(vh) + eps)
+
+
+# ---------------------------------------------------------------- estimator
+def cv_rows(f_cheap, f_paired, y_paired):
+    """Rows z_i = mean_j f(x_j) + Y_i - f(x_i) (their mean is the control-variate estimate)."""
+    return np.mean(f_cheap, axis=0)[None, :] + y_paired - f_paired

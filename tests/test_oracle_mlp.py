@@ -1,0 +1,99 @@
+"""Pins of the oracle's control variate: features against the plain DFT definition,
+backpropagation against central finite differences, Adam against its closed form on a
+quadratic, and the estimator's identities (no GPU)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+
+def test_kset_half_space_and_shells():
+    ks = mlp.kset(10)
+    assert len(ks) == len({tuple(k) for k in ks})
+    assert all(0 < (k ** 2).sum() <= 10 for k in ks)
+    full = {tuple(k) for k in ks} | {tuple(-k) for k in ks}
+    # every nonzero m with |m|^2 <= 10 appears exactly once up to sign
+    r = 3
+    cnt = sum(1 for a in range(-r, r + 1) for b in range(-r, r + 1) for c in range(-r, r + 1)
+              if 0 < a * a + b * b + c * c <= 10)
+    assert len(full) == cnt == 2 * len(ks)
+
+
+def test_features_match_direct_dft():
+    n, h = 8, 0.7
+    rng = np.random.default_rng(0)
+    zb = rng.choice([-1.0, 1.0], size=(n, n, n)) / np.sqrt(h ** 3)
+    phi = rng.normal(size=(n, n, n))
+    a = mlp.features(zb, phi, n, h, 5)
+    b = mlp.features_direct(zb, phi, n, h, 5)
+    assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
+
+
+def test_backprop_matches_finite_differences():
+    rng = np.random.default_rng(1)
+    p = mlp.init_params(7, 9, 5, seed=2)
+    x = rng.normal(size=(6, 7))
+    t = rng.normal(size=(6, 5))
+    loss, g = mlp.loss_and_grads(p, x, t)
+    eps = 1e-6
+    for i in range(8):
+        flat = p[i].reshape(-1)
+        for j in rng.choice(flat.size, size=min(5, flat.size), replace=False):
+            old = flat[j]
+            flat[j] = old + eps
+            lp, _ = mlp.loss_and_grads(p, x, t)
+            flat[j] = old - eps
+            lm, _ = mlp.loss_and_grads(p, x, t)
+            flat[j] = old
+            fd = (lp - lm) / (2 * eps)
+            assert abs(g[i].reshape(-1)[j] - fd) < 1e-6 * max(1.0, abs(fd)) + 1e-9
+
+
+def test_adam_first_step_is_signed_lr():
+    """Bias correction makes the first Adam step -lr * g / (|g| + eps') elementwise."""
+    p = [np.array([1.0, -2.0, 3.0])]
+    g = [np.array([0.5, -4.0, 1e-3])]
+    m = [np.zeros(3)]
+    v = [np.zeros(3)]
+    mlp.adam_step(p, g, m, v, 1, lr=0.01)
+    want = np.array([1.0, -2.0, 3.0]) - 0.01 * g[0] / (np.abs(g[0]) + 1e-8)
+    assert np.allclose(p[0], want, atol=1e-12)
+
+
+def test_adam_minimises_a_quadratic():
+    p = [np.array([3.0, -1.0])]
+    m, v = [np.zeros(2)], [np.zeros(2)]
+    for s in range(1, 3001):
+        mlp.adam_step(p, [2 * (p[0] - np.array([0.5, 0.25]))], m, v, s, lr=0.01)
+    assert np.allclose(p[0], [0.5, 0.25], atol=1e-3)
+
+
+def test_cv_rows_identities():
+    rng = np.random.default_rng(3)
+    Y = rng.normal(size=(20, 4))
+    assert np.array_equal(mlp.cv_rows(np.zeros((50, 4)), np.zeros((20, 4)), Y), Y)
+    # with a perfect predictor the rows are the mean of the cheap predictions
+    f = Y.copy()
+    rows = mlp.cv_rows(Y, f, Y)
+    assert np.allclose(rows, Y.mean(axis=0))
+
+
+def test_cv_estimator_unbiased_and_variance_reduced():
+    """Y = q(x) + e with a predictor f ~ q: the CV mean equals E[Y] within its SE and its
+    per-row spread is that of Y - f."""
+    rng = np.random.default_rng(4)
+    q = lambda x: (x ** 2).sum(axis=1, keepdims=True)
+    est, ses, plain_se = [], [], []
+    for rep in range(200):
+        xc = rng.normal(size=(400, 3))
+        xp = rng.normal(size=(20, 3))
+        y = q(xp) + 0.3 * rng.normal(size=(20, 1))
+        f = lambda x: 0.9 * q(x)
+        rows = mlp.cv_rows(f(xc), f(xp), y)
+        est.append(rows.mean())
+        ses.append(rows.std(ddof=1) / np.sqrt(20))
+        plain_se.append(y.std(ddof=1) / np.sqrt(20))
+    est = np.array(est)
+    # E[Y] = 3; the spread of the estimates matches the SE of Y - f plus Var(f)/M
+    assert abs(est.mean() - 3.0) < 4 * est.std() / np.sqrt(len(est))
+    assert np.mean(ses) < 0.5 * np.mean(plain_se)
