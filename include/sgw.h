@@ -245,6 +245,83 @@ sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_
                          double vxc, double window, double step, int fp64,
                          double* result_host);
 
+/* ----------------------------------------------------------------------------------------
+ * Learned control variate around the plain estimator of Sigma_c(t) (Eq. 4-5).  A sample's
+ * Sigma_i(t) is a quadratic form in its random vector zeta-bar_i, so a network of cheap
+ * features of zeta-bar_i predicts part of it; the paired estimator
+ *   Sigma-hat = mean_{j<M} f(x_j) + mean_{i<n} (Y_i - f(x_i))
+ * over M cheap samples (features only) and n full samples stays unbiased for any f.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Number of features for shells 0 < |m|^2 <= m2max: 2 * (number of +-m pairs + 1). */
+int sgw_cv_feature_count(int m2max);
+
+/*
+ * Features of n_samples Monte-Carlo samples from their white-noise vectors noise_dev
+ * [n_samples][n_vec][N_g] c64 (vector 0 = zeta-bar, 1..n_vec-1 = eta-bar_l, as drawn by
+ * sgw_white_noise).  For a vector v, F_v(k) = dV sum_r Re v(r) phi(r) e^{-i k.r} at k = 2 pi m / L
+ * for 0 < |m|^2 <= m2max (one of each +-m pair: first non-zero component of m positive;
+ * ordered by |m|^2, then (mx, my, mz) lexicographically), weighted by sqrt(4 pi)/|k|.
+ * feat_dev[s] (float, sgw_cv_feature_count(m2max) entries) = [|F_zeta(k)|^2 for each k,
+ * F_zeta(0)^2, sum_l |F_eta_l(k)|^2 for each k, sum_l F_eta_l(0)^2].  Requires n_vec <= max_batch.
+ */
+sgw_status sgw_cv_features(sgw_ctx* ctx, const void* noise_dev, int n_samples, int n_vec, const float* phi_dev,
+                           int m2max, float* feat_dev);
+
+/* Column means and sample standard deviations (FP64; 1 where zero) of y_dev [n_rows][n_out]
+ * (double) into mu_dev, sd_dev when compute_stats != 0, and t_dev = (y - mu) / sd as float. */
+sgw_status sgw_cv_standardize(sgw_ctx* ctx, const double* y_dev, int n_rows, int n_out, int compute_stats,
+                              double* mu_dev, double* sd_dev, float* t_dev);
+
+/* The same for float columns, in place: x = (x - mu) / sd. */
+sgw_status sgw_cv_standardize_f32(sgw_ctx* ctx, float* x_dev, int n_rows, int n_cols, int compute_stats,
+                                  double* mu_dev, double* sd_dev);
+
+/*
+ * Control-variate rows (FP64): rows_dev[i][o] = mean_j f_j[o] + y_i[o] - f_i[o] with
+ * f = mu + sd * (network output), f_cheap_dev [n_cheap][n_out] and f_paired_dev [n_paired][n_out]
+ * the network outputs (float) of the cheap and of the paired samples, y_paired_dev the paired
+ * samples' targets (double).  The mean of the rows is the control-variate estimate and their
+ * spread its sample standard deviation, so they can be passed to sgw_qp_energy as the samples of
+ * Sigma(t) (viewing each complex128 Sigma row as 2 (2 N + 1) doubles).  n_cheap = 0 means f = 0:
+ * the rows are then exactly y (the plain estimator).
+ */
+sgw_status sgw_cv_rows(sgw_ctx* ctx, const float* f_cheap_dev, int n_cheap, const float* f_paired_dev,
+                       const double* y_paired_dev, int n_paired, int n_out, const double* mu_dev,
+                       const double* sd_dev, double* rows_dev);
+
+/*
+ * The network: h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2), h3 = tanh(h2 W3 + b3),
+ * y = h3 W4 + b4, with n_in inputs, three hidden layers of `width`, n_out outputs.  FP32 master
+ * weights and Adam state; the matrix products run on the tensor cores with BF16 operands
+ * (weights, activations, back-propagated errors) and FP32 accumulation.  Loss: mean over the
+ * batch and outputs of (y - t)^2.  Parameters are ordered W1, b1, W2, b2, W3, b3, W4, b4, each
+ * matrix row-major [in][out].  Initial weights U(-1/sqrt(fan_in), 1/sqrt(fan_in)) from
+ * splitmix64(seed), biases 0.  max_batch bounds M in every call.
+ */
+typedef struct sgw_mlp sgw_mlp;
+sgw_status sgw_mlp_create(sgw_mlp** out, int n_in, int width, int n_out, int max_batch, uint64_t seed,
+                          int device, void* stream);
+void sgw_mlp_destroy(sgw_mlp* m);
+const char* sgw_mlp_last_error(const sgw_mlp* m);
+int64_t sgw_mlp_param_count(const sgw_mlp* m);
+/* Replace the parameters (host float array of sgw_mlp_param_count entries); resets Adam. */
+sgw_status sgw_mlp_set_params(sgw_mlp* m, const float* params_host, int64_t n);
+sgw_status sgw_mlp_get_params(sgw_mlp* m, float* params_host, int64_t n);
+/* Per-output loss weights w_o (loss = sum_o w_o (y - t)^2 / (M n_out)); NULL restores 1. */
+sgw_status sgw_mlp_set_loss_weights(sgw_mlp* m, const float* w_host, int n_out);
+/* y_dev [M][n_out] = network(x_dev [M][n_in]) (float). */
+sgw_status sgw_mlp_forward(sgw_mlp* m, const float* x_dev, int M, float* y_dev);
+/* Loss and gradients for a batch (kept for sgw_mlp_adam_step); loss_host and grads_host
+ * (sgw_mlp_param_count floats) are optional and synchronise when given. */
+sgw_status sgw_mlp_gradients(sgw_mlp* m, const float* x_dev, const float* t_dev, int M, double* loss_host,
+                             float* grads_host);
+/* One Adam step (Kingma & Ba; beta1 0.9, beta2 0.999, eps 1e-8) with the last gradients. */
+sgw_status sgw_mlp_adam_step(sgw_mlp* m, float lr);
+/* One pass over n_rows rows in consecutive mini-batches of `batch` (gradients + Adam each). */
+sgw_status sgw_mlp_train_epoch(sgw_mlp* m, const float* x_dev, const float* t_dev, int n_rows, int batch,
+                               float lr, double* mean_loss_host);
+
 /*
  * QP solve that allocates nothing (no counterpart in the paper).  For callers that cannot let
  * a library allocate device memory -- e.g. a host application that has reserved the device's

@@ -7,11 +7,12 @@ The paper has no learned part; this is the control variate the hot path adds aro
 plain sROI estimator (a sample's Sigma_i(t) is a quadratic form in its random vector
 zeta-bar_i, Eq. 4-5, so cheap functions of zeta-bar predict part of it):
 
-* features of a sample: the Fourier coefficients F(k) = sum_r s(r) e^{-i k.r} dV of the
-  source s = zeta-bar * phi on the shells 0 < |m|^2 <= m2max (k = 2 pi m / L, one of each
-  +-k pair, the half space whose first non-zero component of m is positive), each weighted
-  by sqrt(4 pi)/|k| (the Coulomb kernel's square root), as real and imaginary parts; then
-  F(0) = <phi|zeta-bar> (real part);
+* features of a sample: for a random vector v and the orbital phi, F_v(k) = dV sum_r
+  v(r) phi(r) e^{-i k.r} on the shells 0 < |m|^2 <= m2max (k = 2 pi m / L, one of each +-k
+  pair: the first non-zero component of m positive) weighted by sqrt(4 pi)/|k|; the features
+  are |F_zeta(k)|^2 for each k and F_zeta(0)^2 for zeta-bar, then sum_l |F_eta_l(k)|^2 and
+  sum_l F_eta_l(0)^2 over the sample's eta-bar_l (these drive the fluctuations of the
+  Coulomb-weighted quadratic forms behind Sigma_i and the exchange X_i);
 * network: layers h_1 = tanh(x W1 + b1), h_2 = tanh(h_1 W2 + b2), h_3 = tanh(h_2 W3 + b3),
   y = h_3 W4 + b4; loss = mean over samples and outputs of (y - t)^2; Adam;
 * estimator: with M cheap samples (features only) and n paired samples (features and the
@@ -38,39 +39,43 @@ def kset(m2max):
     return np.array(sorted(out, key=lambda m: (m[0] ** 2 + m[1] ** 2 + m[2] ** 2, m)), dtype=np.int64)
 
 
-def features(zbar, phi, n, h, m2max):
-    """Feature vector of one sample (zbar, phi: [n, n, n] real arrays indexed [z, y, x]).
+def coeffs(v, phi, n, h, m2max):
+    """Coulomb-weighted coefficients sqrt(4 pi)/|k| F_v(k) on the k list, and F_v(0), by FFT.
 
-    m = (mx, my, mz); F(m) = dV sum_r s(r) exp(-2 pi i (mx x + my y + mz z) / n) by FFT.
+    F_v(m) = dV sum_r v phi exp(-2 pi i (mx x + my y + mz z) / n); arrays indexed [z, y, x].
     """
-    s = zbar * phi
-    dV = h ** 3
+    F = np.fft.fftn(v * phi) * h ** 3          # F[mz, my, mx]
     L = n * h
-    F = np.fft.fftn(s) * dV            # axes (z, y, x): F[mz, my, mx]
     ks = kset(m2max)
-    vals = []
-    for mx, my, mz in ks:
-        kk = 2 * np.pi / L * np.sqrt(mx * mx + my * my + mz * mz)
-        vals.append(F[mz % n, my % n, mx % n] * np.sqrt(4 * np.pi) / kk)
-    vals = np.array(vals)
-    return np.concatenate([vals.real, vals.imag, [F[0, 0, 0].real]])
+    c = np.array([F[mz % n, my % n, mx % n] * np.sqrt(4 * np.pi) / (2 * np.pi / L * np.sqrt(mx * mx + my * my + mz * mz))
+                  for mx, my, mz in ks])
+    return c, F[0, 0, 0].real
 
 
-def features_direct(zbar, phi, n, h, m2max):
-    """Same features by the plain DFT sum (no FFT), for pinning `features` on tiny grids."""
-    s = zbar * phi
-    dV = h ** 3
+def coeffs_direct(v, phi, n, h, m2max):
+    """Same coefficients by the plain DFT sum (no FFT), for pinning `coeffs` on tiny grids."""
+    s = v * phi
     L = n * h
     idx = np.arange(n)
     Z, Y, X = np.meshgrid(idx, idx, idx, indexing='ij')
-    ks = kset(m2max)
-    vals = []
-    for mx, my, mz in ks:
+    c = []
+    for mx, my, mz in kset(m2max):
         ph = np.exp(-2j * np.pi * (mx * X + my * Y + mz * Z) / n)
-        kk = 2 * np.pi / L * np.sqrt(mx * mx + my * my + mz * mz)
-        vals.append(dV * np.sum(s * ph) * np.sqrt(4 * np.pi) / kk)
-    vals = np.array(vals)
-    return np.concatenate([vals.real, vals.imag, [dV * np.sum(s)]])
+        c.append(h ** 3 * np.sum(s * ph) * np.sqrt(4 * np.pi) / (2 * np.pi / L * np.sqrt(mx * mx + my * my + mz * mz)))
+    return np.array(c), h ** 3 * np.sum(s)
+
+
+def features(zbar, etabars, phi, n, h, m2max):
+    """[|F_zeta(k)|^2 ..., F_zeta(0)^2, sum_l |F_eta_l(k)|^2 ..., sum_l F_eta_l(0)^2]."""
+    cz, z0 = coeffs(zbar, phi, n, h, m2max)
+    ce = [coeffs(e, phi, n, h, m2max) for e in etabars]
+    se = np.sum([np.abs(c) ** 2 for c, _ in ce], axis=0)
+    s0 = np.sum([e0 ** 2 for _, e0 in ce])
+    return np.concatenate([np.abs(cz) ** 2, [z0 ** 2], se, [s0]])
+
+
+def feature_count(m2max):
+    return 2 * (len(kset(m2max)) + 1)
 
 
 # ---------------------------------------------------------------- network
@@ -99,12 +104,13 @@ def forward(p, x):
     return a, (acts, pre)
 
 
-def loss_and_grads(p, x, t):
-    """Mean-squared loss over all M x n_out entries and its gradients (backpropagation)."""
+def loss_and_grads(p, x, t, w=None):
+    """Loss sum_o w_o (y - t)^2 / (M n_out) (w = 1 by default) and its gradients (backpropagation)."""
     y, (acts, pre) = forward(p, x)
     M, O = y.shape
-    loss = np.mean((y - t) ** 2)
-    d = 2.0 * (y - t) / (M * O)
+    w = np.ones(O) if w is None else np.asarray(w, dtype=np.float64)
+    loss = np.mean(w * (y - t) ** 2)
+    d = 2.0 * w * (y - t) / (M * O)
     g = [None] * 8
     for i in reversed(range(4)):
         if i < 3:
@@ -126,6 +132,15 @@ def adam_step(p, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
 
 
 # ---------------------------------------------------------------- estimator
+def standardize(a, mu=None, sd=None):
+    """Column statistics (sample standard deviation; 1 where it is zero) and (a - mu) / sd."""
+    if mu is None:
+        mu = a.mean(axis=0)
+        sd = a.std(axis=0, ddof=1) if a.shape[0] > 1 else np.zeros(a.shape[1])
+        sd = np.where(sd > 0, sd, 1.0)
+    return (a - mu) / sd, mu, sd
+
+
 def cv_rows(f_cheap, f_paired, y_paired):
     """Rows z_i = mean_j f(x_j) + Y_i - f(x_i) (their mean is the control-variate estimate)."""
     return np.mean(f_cheap, axis=0)[None, :] + y_paired - f_paired

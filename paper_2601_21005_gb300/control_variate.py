@@ -1,0 +1,135 @@
+"""Learned control variate for the stochastic Sigma_c(t) and X (the product path, through the C ABI).
+
+A sample's Sigma_i(t) (Eq. 5) and its sROI exchange X_i (Eq. 6) are quadratic forms in the
+sample's random vectors (zeta-bar_i and the eta-bar_il), so cheap features of those vectors --
+the Coulomb-weighted low-k power of zeta-bar_i phi and of eta-bar_il phi -- predict part of them.
+The steps:
+
+  collect : run plain samples (Pipeline.run_batch); targets Y_i = [Sigma_i(t) (2 (2N + 1) reals),
+            X_i], features x_i of the same samples;
+  train   : standardise inputs and targets (FP64 statistics), fit the network (GPU forward,
+            backward, Adam), keep the epoch with the lowest loss on a held-out part;
+  estimate: with n new paired samples (Y_i, x_i) and M cheap samples (features only: the same
+            Philox vectors of sample indices never run through the plain path), form the rows
+            z_i = mean_j f(x_j) + Y_i - f(x_i) (FP64) and solve the QP equation on them.  The
+            estimate is unbiased for any network; with no cheap samples it is the plain one.
+"""
+import numpy as np
+
+from . import sgw as _sgw
+
+
+class ControlVariate:
+    def __init__(self, pipeline, m2max=10, width=256, seed=77, max_batch=256):
+        import torch
+        self.torch = torch
+        self.pl = pipeline
+        self.m2max = m2max
+        self.n_feat = _sgw.sgw_cv_feature_count(m2max)
+        self.n_sig = 2 * (2 * pipeline.n_steps + 1)
+        self.n_out = self.n_sig + 1
+        self.max_batch = max_batch
+        self.mlp = _sgw.MLP(self.n_feat, width, self.n_out, max_batch, seed=seed, device=pipeline.dev.index or 0)
+        # X is one output against 2 (2N + 1) for Sigma(t) but carries a comparable share of the
+        # QP variance: give it half the weight of the whole Sigma block.
+        w = np.ones(self.n_out, dtype=np.float32)
+        w[-1] = 0.5 * self.n_sig
+        self.mlp.set_loss_weights(w)
+        dev = pipeline.dev
+        f64 = torch.float64
+        self.mu = torch.zeros(self.n_out, dtype=f64, device=dev)
+        self.sd = torch.ones(self.n_out, dtype=f64, device=dev)
+        self.mu_x = torch.zeros(self.n_feat, dtype=f64, device=dev)
+        self.sd_x = torch.ones(self.n_feat, dtype=f64, device=dev)
+        self._noise = None
+
+    # -------------------------------------------------------------- data
+    def collect(self, n_samples, sample0):
+        """Plain samples sample0.. : (Y [n][n_out] f64 = [Sigma(t) interleaved, X], F [n][n_feat] f32)."""
+        t, pl = self.torch, self.pl
+        ns = pl.ns
+        nb = (n_samples + ns - 1) // ns
+        S = t.empty(nb * ns, 2 * pl.n_steps + 1, dtype=t.complex128, device=pl.dev)
+        X = t.empty(nb * ns, dtype=t.float64, device=pl.dev)
+        F = t.empty(nb * ns, self.n_feat, dtype=t.float32, device=pl.dev)
+        for b in range(nb):
+            s0 = b * ns
+            pl.run_batch(sample0 + s0, S[s0:s0 + ns], X[s0:s0 + ns])
+            pl.ctx.cv_features(pl.noise, ns, pl.n_eta + 1, pl.phi, self.m2max, F[s0:s0 + ns])
+        Y = t.cat([t.view_as_real(S).reshape(nb * ns, -1), X[:, None]], dim=1)[:n_samples].contiguous()
+        return Y, F[:n_samples].contiguous()
+
+    def cheap_features(self, n_samples, sample0):
+        """Features of samples sample0.. from their white noise alone (no filter, no propagation)."""
+        t, pl = self.torch, self.pl
+        nv = pl.n_eta + 1
+        chunk = max(1, pl.ctx.max_batch // nv)
+        if self._noise is None:
+            self._noise = t.empty(chunk * nv, pl.ng, dtype=t.complex64, device=pl.dev)
+        F = t.empty(n_samples, self.n_feat, dtype=t.float32, device=pl.dev)
+        for s0 in range(0, n_samples, chunk):
+            m = min(chunk, n_samples - s0)
+            pl.ctx.white_noise(pl.seed, pl.stream_id, sample0 + s0, m, nv, self._noise)
+            pl.ctx.cv_features(self._noise, m, nv, pl.phi, self.m2max, F[s0:s0 + m])
+        return F
+
+    # -------------------------------------------------------------- network
+    def train(self, F, Y, epochs=300, batch=64, lr=1e-3, holdout=0.2):
+        """Standardise and fit; the parameters of the epoch with the lowest held-out loss are kept.
+        Returns (training losses, held-out losses)."""
+        t, ctx = self.torch, self.pl.ctx
+        n = F.shape[0]
+        nv = max(1, int(round(holdout * n))) if n > 4 else 0
+        ntr = n - nv
+        Fs = F.clone()
+        ctx.cv_standardize_f32(Fs[:ntr], self.mu_x, self.sd_x, True)
+        if nv:
+            ctx.cv_standardize_f32(Fs[ntr:], self.mu_x, self.sd_x, False)
+        T = t.empty(Y.shape, dtype=t.float32, device=Y.device)
+        ctx.cv_standardize(Y[:ntr].contiguous(), self.mu, self.sd, T[:ntr], True)
+        if nv:
+            ctx.cv_standardize(Y[ntr:].contiguous(), self.mu, self.sd, T[ntr:], False)
+        bs = min(batch, self.max_batch)
+        tr_l, va_l = [], []
+        best, best_p = float('inf'), None
+        for _ in range(epochs):
+            tr_l.append(self.mlp.train_epoch(Fs[:ntr], T[:ntr], bs, lr))
+            if nv:
+                vl, _ = self.mlp.gradients(Fs[ntr:ntr + min(nv, self.max_batch)],
+                                           T[ntr:ntr + min(nv, self.max_batch)])
+                va_l.append(vl)
+                if vl < best:
+                    best, best_p = vl, self.mlp.get_params()
+        if best_p is not None:
+            self.mlp.set_params(best_p)
+        return tr_l, va_l
+
+    def predict(self, F):
+        """Network outputs (standardised units) for raw features F."""
+        t = self.torch
+        Fs = F.clone()
+        self.pl.ctx.cv_standardize_f32(Fs, self.mu_x, self.sd_x, False)
+        out = t.empty(F.shape[0], self.n_out, dtype=t.float32, device=F.device)
+        for s0 in range(0, F.shape[0], self.max_batch):
+            m = min(self.max_batch, F.shape[0] - s0)
+            self.mlp.forward(Fs[s0:s0 + m].contiguous(), out[s0:s0 + m])
+        return out
+
+    # -------------------------------------------------------------- estimator
+    def rows(self, F_cheap, F_paired, Y_paired):
+        """Control-variate rows: (Sigma rows [n][2N+1] complex128, X rows [n] f64)."""
+        t = self.torch
+        rows = t.empty_like(Y_paired)
+        if F_cheap is None:
+            self.pl.ctx.cv_rows(None, None, Y_paired, None, None, rows)
+        else:
+            self.pl.ctx.cv_rows(self.predict(F_cheap), self.predict(F_paired), Y_paired, self.mu, self.sd, rows)
+        n = rows.shape[0]
+        sig = t.view_as_complex(rows[:, :self.n_sig].contiguous().reshape(n, -1, 2)).contiguous()
+        return sig, rows[:, self.n_sig].contiguous()
+
+    def plain_rows(self, Y_paired):
+        n = Y_paired.shape[0]
+        t = self.torch
+        return (t.view_as_complex(Y_paired[:, :self.n_sig].contiguous().reshape(n, -1, 2)).contiguous(),
+                Y_paired[:, self.n_sig].contiguous())

@@ -1086,6 +1086,104 @@ sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_
     return SGW_OK;
 }
 
+// Wave vectors m, 0 < |m|^2 <= m2max, one of each +-m pair (first non-zero component > 0),
+// ordered by |m|^2 and then lexicographically (mx, my, mz).
+static std::vector<int4> cv_kset(int m2max) {
+    std::vector<int4> ks;
+    const int r = (int)std::floor(std::sqrt((double)m2max));
+    for (int a = -r; a <= r; ++a)
+        for (int b = -r; b <= r; ++b)
+            for (int c = -r; c <= r; ++c) {
+                const int n2 = a * a + b * b + c * c;
+                if (n2 == 0 || n2 > m2max) continue;
+                const int first = a != 0 ? a : (b != 0 ? b : c);
+                if (first > 0) ks.push_back(make_int4(a, b, c, n2));
+            }
+    std::sort(ks.begin(), ks.end(), [](const int4& p, const int4& q) {
+        if (p.w != q.w) return p.w < q.w;
+        if (p.x != q.x) return p.x < q.x;
+        if (p.y != q.y) return p.y < q.y;
+        return p.z < q.z;
+    });
+    return ks;
+}
+
+int sgw_cv_feature_count(int m2max) { return m2max < 1 ? 2 : 2 * ((int)cv_kset(m2max).size() + 1); }
+
+sgw_status sgw_cv_features(sgw_ctx* ctx, const void* noise_dev, int n_samples, int n_vec, const float* phi_dev,
+                           int m2max, float* feat_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 0 || n_vec < 1 || m2max < 1) return fail(ctx, SGW_EINVAL, "bad feature arguments");
+    if (n_samples == 0) return SGW_OK;
+    if (!noise_dev || !phi_dev || !feat_dev) return fail(ctx, SGW_EINVAL, "null feature pointers");
+    const std::vector<int4> ks = cv_kset(m2max);
+    const int nk = (int)ks.size();
+    const int chunk = std::max(1, ctx->max_batch / n_vec);
+    if (n_vec > ctx->max_batch) return fail(ctx, SGW_EINVAL, "n_vec must not exceed max_batch");
+    void *p, *q;
+    if ((s = work(ctx, 6, sizeof(int4) * nk, &p))) return s;
+    if ((s = work(ctx, 7, sizeof(float) * (size_t)chunk * n_vec * (2 * nk + 1), &q))) return s;
+    int4* ksd = (int4*)p;
+    float* raw = (float*)q;
+    CK(cudaMemcpyAsync(ksd, ks.data(), sizeof(int4) * nk, cudaMemcpyHostToDevice, ctx->stream));
+    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
+    for (int s0 = 0; s0 < n_samples; s0 += chunk) {
+        const int ns = std::min(chunk, n_samples - s0);
+        const int nvv = ns * n_vec;
+        Launch L(ctx, SGW_PROF_OTHER, 4);
+        sgw::launch_cv_source(ctx->ng, (const float2*)noise_dev + (size_t)s0 * n_vec * ctx->ng, ctx->ng, phi_dev, nvv,
+                              ctx->B1, ctx->stream);
+        sgw::launch_plane_fwd(ctx->n, ctx->B1, ctx->W, nvv, ctx->tw, ctx->stream);
+        sgw::launch_cv_gather(ctx->n, ctx->W, nvv, nk, ksd, kscale, (float)ctx->dV, ctx->tw, raw, ctx->stream);
+        sgw::launch_cv_combine(ns, n_vec, nk, raw, feat_dev + (size_t)s0 * 2 * (nk + 1), ctx->stream);
+        CKL();
+    }
+    // the host list must outlive the (pageable, stream-ordered) copy
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SGW_OK;
+}
+
+sgw_status sgw_cv_standardize(sgw_ctx* ctx, const double* y_dev, int n_rows, int n_out, int compute_stats,
+                              double* mu_dev, double* sd_dev, float* t_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_rows < 1 || n_out < 1 || !y_dev || !mu_dev || !sd_dev || !t_dev)
+        return fail(ctx, SGW_EINVAL, "bad standardize arguments");
+    Launch L(ctx, SGW_PROF_OTHER, 2);
+    if (compute_stats) sgw::launch_cv_stats(n_rows, n_out, y_dev, mu_dev, sd_dev, ctx->stream);
+    sgw::launch_cv_standardize((int64_t)n_rows * n_out, n_out, y_dev, mu_dev, sd_dev, t_dev, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_cv_standardize_f32(sgw_ctx* ctx, float* x_dev, int n_rows, int n_cols, int compute_stats,
+                                  double* mu_dev, double* sd_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_rows < 1 || n_cols < 1 || !x_dev || !mu_dev || !sd_dev)
+        return fail(ctx, SGW_EINVAL, "bad standardize arguments");
+    Launch L(ctx, SGW_PROF_OTHER, 2);
+    sgw::launch_cv_standardize_f32(n_rows, n_cols, x_dev, mu_dev, sd_dev, compute_stats, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_cv_rows(sgw_ctx* ctx, const float* f_cheap_dev, int n_cheap, const float* f_paired_dev,
+                       const double* y_paired_dev, int n_paired, int n_out, const double* mu_dev,
+                       const double* sd_dev, double* rows_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_cheap < 0 || n_paired < 1 || n_out < 1 || !y_paired_dev || !rows_dev ||
+        (n_cheap > 0 && (!f_cheap_dev || !f_paired_dev || !mu_dev || !sd_dev)))
+        return fail(ctx, SGW_EINVAL, "bad control-variate arguments");
+    Launch L(ctx, SGW_PROF_OTHER);
+    sgw::launch_cv_rows(n_cheap, n_paired, n_out, f_cheap_dev, f_paired_dev, y_paired_dev, mu_dev, sd_dev, rows_dev,
+                        ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
 sgw_status sgw_profile(sgw_ctx* ctx, int enable) {
     sgw_status s = check_ctx(ctx, false);
     if (s) return s;

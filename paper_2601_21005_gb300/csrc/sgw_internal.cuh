@@ -124,6 +124,18 @@ void launch_qp(const double* sigma, const double* x, int n_samples, int n_steps,
                int n_scan, double* result, cudaStream_t st);
 int time_order_threads(int M);
 void set_global_error(const char* msg);
+// control variate (kernels_mlp.cu)
+void launch_cv_source(int64_t ng, const float2* zb, int64_t stride, const float* phi, int n_samples, float2* out,
+                      cudaStream_t st);
+void launch_cv_gather(int n, const float2* W, int n_samples, int nk, const int4* ks, float kscale, float dV,
+                      const float2* tw, float* feat, cudaStream_t st);
+void launch_cv_stats(int n, int O, const double* y, double* mu, double* sd, cudaStream_t st);
+void launch_cv_combine(int n_samples, int nv, int nk, const float* raw, float* feat, cudaStream_t st);
+void launch_cv_standardize_f32(int n, int O, float* y, double* mu, double* sd, int compute, cudaStream_t st);
+void launch_cv_standardize(int64_t total, int O, const double* y, const double* mu, const double* sd, float* t,
+                           cudaStream_t st);
+void launch_cv_rows(int Mc, int n, int O, const float* fc, const float* fp, const double* y, const double* mu,
+                    const double* sd, double* rows, cudaStream_t st);
 void launch_prepare(int ng, const float2* noise, const float2* filt, const float* phi, int n_samples, int n_eta,
                     float2* eta, float2* zeta, float* source, cudaStream_t st);
 

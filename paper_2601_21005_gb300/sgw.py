@@ -49,6 +49,22 @@ _SIGS = {
     'sgw_sigma_c': ([_P, _P, _P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_exchange': ([_P, _P, _P, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_sigma_omega': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _P, _c.c_int, _c.c_int, _P], _c.c_int),
+    'sgw_cv_feature_count': ([_c.c_int], _c.c_int),
+    'sgw_cv_features': ([_P, _P, _c.c_int, _c.c_int, _P, _c.c_int, _P], _c.c_int),
+    'sgw_cv_standardize': ([_P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P], _c.c_int),
+    'sgw_cv_standardize_f32': ([_P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P], _c.c_int),
+    'sgw_cv_rows': ([_P, _P, _c.c_int, _P, _P, _c.c_int, _c.c_int, _P, _P, _P], _c.c_int),
+    'sgw_mlp_create': ([_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64, _c.c_int, _P], _c.c_int),
+    'sgw_mlp_destroy': ([_P], None),
+    'sgw_mlp_last_error': ([_P], _c.c_char_p),
+    'sgw_mlp_param_count': ([_P], _c.c_int64),
+    'sgw_mlp_set_params': ([_P, _P, _c.c_int64], _c.c_int),
+    'sgw_mlp_get_params': ([_P, _P, _c.c_int64], _c.c_int),
+    'sgw_mlp_forward': ([_P, _P, _c.c_int, _P], _c.c_int),
+    'sgw_mlp_set_loss_weights': ([_P, _P, _c.c_int], _c.c_int),
+    'sgw_mlp_gradients': ([_P, _P, _P, _c.c_int, _P, _P], _c.c_int),
+    'sgw_mlp_adam_step': ([_P, _c.c_float], _c.c_int),
+    'sgw_mlp_train_epoch': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_float, _P], _c.c_int),
     'sgw_qp_energy_noalloc': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double, _c.c_double,
                                _c.c_double, _c.c_double, _c.c_int, _P, _P], _c.c_int),
     'sgw_profile': ([_P, _c.c_int], _c.c_int),
@@ -140,6 +156,81 @@ def sgw_qp_energy_noalloc(sigma, x, n_samples, n_steps, dt, gamma, eps_ks, vxc=0
            lib().sgw_qp_energy_noalloc(_dev(sigma, torch.complex128), _dev(x, torch.float64), n_samples, n_steps, dt,
                                        gamma, eps_ks, vxc, window, step, fp64, r.ctypes.data_as(_P), _P(stream)))
     return dict(eps_qp=r[0], se=r[1], re_sigma=r[2], z=r[3])
+
+
+def sgw_cv_feature_count(m2max):
+    return lib().sgw_cv_feature_count(m2max)
+
+
+class MLP:
+    """Owns one sgw_mlp (the control-variate network).  Methods mirror sgw_mlp_*."""
+
+    def __init__(self, n_in, width, n_out, max_batch, seed=0, device=0, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        p = _P()
+        _check('sgw_mlp_create', lib().sgw_mlp_create(ctypes.byref(p), n_in, width, n_out, max_batch, seed, device,
+                                                      _P(stream)))
+        self._p = p
+        self.n_in, self.width, self.n_out, self.max_batch = n_in, width, n_out, max_batch
+
+    def close(self):
+        if getattr(self, '_p', None):
+            lib().sgw_mlp_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, fn, st):
+        if st != 0:
+            msg = lib().sgw_mlp_last_error(self._p)
+            raise SgwError(fn, st, msg.decode() if msg else '')
+
+    def param_count(self):
+        return lib().sgw_mlp_param_count(self._p)
+
+    def set_params(self, flat):
+        a, pa = _host(flat, np.float32)
+        self._ck('sgw_mlp_set_params', lib().sgw_mlp_set_params(self._p, pa, len(a)))
+
+    def get_params(self):
+        out = np.zeros(self.param_count(), dtype=np.float32)
+        self._ck('sgw_mlp_get_params', lib().sgw_mlp_get_params(self._p, out.ctypes.data_as(_P), len(out)))
+        return out
+
+    def set_loss_weights(self, w):
+        a, pa = _host(w, np.float32)
+        self._ck('sgw_mlp_set_loss_weights', lib().sgw_mlp_set_loss_weights(self._p, pa, self.n_out))
+
+    def forward(self, x, y):
+        import torch
+        self._ck('sgw_mlp_forward', lib().sgw_mlp_forward(self._p, _dev(x, torch.float32), x.shape[0],
+                                                         _dev(y, torch.float32)))
+
+    def gradients(self, x, t, want_grads=False):
+        import torch
+        loss = _c.c_double()
+        g = np.zeros(self.param_count(), dtype=np.float32) if want_grads else None
+        self._ck('sgw_mlp_gradients', lib().sgw_mlp_gradients(self._p, _dev(x, torch.float32), _dev(t, torch.float32),
+                                                             x.shape[0], _c.byref(loss),
+                                                             g.ctypes.data_as(_P) if want_grads else None))
+        return loss.value, g
+
+    def adam_step(self, lr):
+        self._ck('sgw_mlp_adam_step', lib().sgw_mlp_adam_step(self._p, lr))
+
+    def train_epoch(self, x, t, batch, lr):
+        import torch
+        loss = _c.c_double()
+        self._ck('sgw_mlp_train_epoch', lib().sgw_mlp_train_epoch(self._p, _dev(x, torch.float32),
+                                                                 _dev(t, torch.float32), x.shape[0], batch, lr,
+                                                                 _c.byref(loss)))
+        return loss.value
 
 
 # ------------------------------------------------------------------ context
@@ -290,3 +381,30 @@ class Context:
         n = _c.c_int64()
         self._ck('sgw_launch_count', lib().sgw_launch_count(self._p, _c.byref(n)))
         return n.value
+
+    def cv_features(self, noise, n_samples, n_vec, phi, m2max, feat):
+        import torch
+        self._ck('sgw_cv_features', lib().sgw_cv_features(self._p, _dev(noise, torch.complex64), n_samples, n_vec,
+                                                         _dev(phi, torch.float32), m2max, _dev(feat, torch.float32)))
+
+    def cv_standardize(self, y, mu, sd, t, compute_stats=True):
+        import torch
+        self._ck('sgw_cv_standardize', lib().sgw_cv_standardize(self._p, _dev(y, torch.float64), y.shape[0],
+                                                               y.shape[1], 1 if compute_stats else 0,
+                                                               _dev(mu, torch.float64), _dev(sd, torch.float64),
+                                                               _dev(t, torch.float32)))
+
+    def cv_standardize_f32(self, x, mu, sd, compute_stats=True):
+        import torch
+        self._ck('sgw_cv_standardize_f32', lib().sgw_cv_standardize_f32(self._p, _dev(x, torch.float32), x.shape[0],
+                                                                       x.shape[1], 1 if compute_stats else 0,
+                                                                       _dev(mu, torch.float64),
+                                                                       _dev(sd, torch.float64)))
+
+    def cv_rows(self, f_cheap, f_paired, y_paired, mu, sd, rows):
+        import torch
+        nc = 0 if f_cheap is None else f_cheap.shape[0]
+        self._ck('sgw_cv_rows', lib().sgw_cv_rows(self._p, _dev(f_cheap, torch.float32), nc,
+                                                 _dev(f_paired, torch.float32), _dev(y_paired, torch.float64),
+                                                 y_paired.shape[0], y_paired.shape[1], _dev(mu, torch.float64),
+                                                 _dev(sd, torch.float64), _dev(rows, torch.float64)))

@@ -19,14 +19,30 @@ def test_kset_half_space_and_shells():
     assert len(full) == cnt == 2 * len(ks)
 
 
-def test_features_match_direct_dft():
+def test_coefficients_match_direct_dft():
     n, h = 8, 0.7
     rng = np.random.default_rng(0)
     zb = rng.choice([-1.0, 1.0], size=(n, n, n)) / np.sqrt(h ** 3)
     phi = rng.normal(size=(n, n, n))
-    a = mlp.features(zb, phi, n, h, 5)
-    b = mlp.features_direct(zb, phi, n, h, 5)
+    a, a0 = mlp.coeffs(zb, phi, n, h, 5)
+    b, b0 = mlp.coeffs_direct(zb, phi, n, h, 5)
     assert np.max(np.abs(a - b)) < 1e-10 * np.max(np.abs(b))
+    assert abs(a0 - b0) < 1e-10 * abs(b0)
+
+
+def test_features_layout():
+    n, h = 8, 0.7
+    rng = np.random.default_rng(1)
+    v = [rng.choice([-1.0, 1.0], size=(n, n, n)) for _ in range(4)]
+    phi = rng.normal(size=(n, n, n))
+    f = mlp.features(v[0], v[1:], phi, n, h, 5)
+    nk = len(mlp.kset(5))
+    assert len(f) == mlp.feature_count(5) == 2 * (nk + 1)
+    c0, z0 = mlp.coeffs_direct(v[0], phi, n, h, 5)
+    assert np.allclose(f[:nk], np.abs(c0) ** 2) and np.isclose(f[nk], z0 ** 2)
+    ce = [mlp.coeffs_direct(e, phi, n, h, 5) for e in v[1:]]
+    assert np.allclose(f[nk + 1:2 * nk + 1], sum(np.abs(c) ** 2 for c, _ in ce))
+    assert np.isclose(f[-1], sum(e0 ** 2 for _, e0 in ce))
 
 
 def test_backprop_matches_finite_differences():
@@ -34,16 +50,17 @@ def test_backprop_matches_finite_differences():
     p = mlp.init_params(7, 9, 5, seed=2)
     x = rng.normal(size=(6, 7))
     t = rng.normal(size=(6, 5))
-    loss, g = mlp.loss_and_grads(p, x, t)
+    wts = rng.uniform(0.5, 3.0, size=5)
+    loss, g = mlp.loss_and_grads(p, x, t, wts)
     eps = 1e-6
     for i in range(8):
         flat = p[i].reshape(-1)
         for j in rng.choice(flat.size, size=min(5, flat.size), replace=False):
             old = flat[j]
             flat[j] = old + eps
-            lp, _ = mlp.loss_and_grads(p, x, t)
+            lp, _ = mlp.loss_and_grads(p, x, t, wts)
             flat[j] = old - eps
-            lm, _ = mlp.loss_and_grads(p, x, t)
+            lm, _ = mlp.loss_and_grads(p, x, t, wts)
             flat[j] = old
             fd = (lp - lm) / (2 * eps)
             assert abs(g[i].reshape(-1)[j] - fd) < 1e-6 * max(1.0, abs(fd)) + 1e-9
