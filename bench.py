@@ -126,12 +126,12 @@ def kohn_sham_inputs(cfg, sysd, device):
                 raw_bounds=raw, eig_residual=res)
 
 
-def make_pipeline(cfg, sysd, ks, device, seed, fp64=True):
+def make_pipeline(cfg, sysd, ks, device, seed, fp64=True, graphs=False):
     from paper_2601_21005_gb300.pipeline import Pipeline
     return Pipeline(cfg['n'], cfg['h'], sysd['vloc'], sysd['kb_atoms'], ks['phi'], ks['e_homo'], ks['e_lumo'],
                     n_eta=cfg['n_eta'], n_steps=cfg['n_steps'], dt=cfg['dt'], cheb_deg=cfg['cheb_deg'],
                     n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'], seed=seed, stream_id=1,
-                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64)
+                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64, graphs=graphs)
 
 
 def units_per_step(cfg):
@@ -286,7 +286,7 @@ def run_ours(args, cfg):
         ks = kohn_sham_inputs(cfg, sysd, local)
         if args.ks_cache:
             np.savez(args.ks_cache, **{k: np.asarray(v) for k, v in ks.items()})
-    pl = make_pipeline(cfg, sysd, ks, local, seed)
+    pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs)
     t_setup = time.perf_counter() - t_setup
     ns = cfg['samples_per_batch']
     nb_total = args.warmup + args.steps
@@ -305,7 +305,8 @@ def run_ours(args, cfg):
     torch.cuda.synchronize()
     st = torch.cuda.current_stream()
     clocks = ClockSampler(local)
-    pl.ctx.profile(True)
+    if not args.graphs:                # per-launch events would disable the graph replay
+        pl.ctx.profile(True)
     n0 = pl.ctx.launch_count()
     if dist:
         dist.barrier()
@@ -324,8 +325,15 @@ def run_ours(args, cfg):
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
     launches = pl.ctx.launch_count() - n0
-    prof = pl.ctx.profile_read()
-    pl.ctx.profile(False)
+    if args.graphs:
+        # kernel durations from one more step with per-launch events (direct launches)
+        pl.ctx.profile(True)
+        step(0)
+        prof = pl.ctx.profile_read()
+        pl.ctx.profile(False)
+    else:
+        prof = pl.ctx.profile_read()
+        pl.ctx.profile(False)
     if dist:
         t = torch.tensor([ms], device='cuda', dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -360,6 +368,10 @@ def run_ours(args, cfg):
         ms_e2e = float(t.item())
     e2e = dict(value=units_per_step(cfg) * args.steps * world / (ms_e2e * 1e-3), unit=UNIT,
                h2d_bytes_per_step=phi_h.numel() * 4, d2h_bytes_per_step=sig_h.numel() * 16 + x_h.numel() * 8 + 32)
+    # plain FP32 form (Sigma reductions, transform and QP in FP32) on the same samples as the
+    # mixed form (FP64 there): the eV difference of the QP energy
+    prec = precision_comparison(cfg, sysd, ks, local, seed, pl, base)
+    cvres = cv_study(args, cfg, pl, ks, base) if args.cv > 0 else None
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -371,15 +383,82 @@ def run_ours(args, cfg):
                 data='synthetic',
                 config=dict(workload=cfg['workload'], n_cheb=cfg['n_cheb'], cheb_deg=cfg['cheb_deg'], dt=cfg['dt'],
                             samples_per_step=ns * world, l2='inputs larger than L2 (about 5 GB live per batch)',
-                            precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world),
+                            precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world,
+                            cuda_graphs=bool(args.graphs),
+                            roofline_timing='per-kernel CUDA events over the timed region' if not args.graphs else
+                            'per-kernel CUDA events over one extra step (graph replay is timed unprofiled)'),
                 e2e=e2e, gpu_launches=int(launches), roofline=rl, cpu_baseline=cpu,
-                clocks=clk, time_to_0_03eV=tt,
+                clocks=clk, time_to_0_03eV=tt, precision_forms=prec, control_variate=cvres,
                 setup=dict(seconds=round(t_setup, 2), e_homo=ks['e_homo'], e_lumo=ks['e_lumo'],
                            gap_eV=round((ks['e_lumo'] - ks['e_homo']) * HA_EV, 4), emin=ks['emin'], emax=ks['emax'],
                            eig_residual=float(ks['eig_residual'])))
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def precision_comparison(cfg, sysd, ks, device, seed, pl, base):
+    """Run one batch in the plain FP32 form and the same batch in the mixed form; QP difference."""
+    import torch
+    pl32 = make_pipeline(cfg, sysd, ks, device, seed, fp64=False)
+    ns = cfg['samples_per_batch']
+    out = {}
+    for name, p in (('mixed_fp64', pl), ('plain_fp32', pl32)):
+        sg = torch.empty(ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
+        x = torch.empty(ns, dtype=torch.float64, device='cuda')
+        p.run_batch(base + 900000, sg, x)
+        out[name] = p.qp(sg, x, ks['e_homo'])['eps_qp']
+    pl32.ctx.close()
+    return dict(qp_eV_mixed=round(out['mixed_fp64'] * HA_EV, 6), qp_eV_plain_fp32=round(out['plain_fp32'] * HA_EV, 6),
+                diff_eV=abs(out['plain_fp32'] - out['mixed_fp64']) * HA_EV, samples=ns)
+
+
+def cv_study(args, cfg, pl, ks, base):
+    """Train the control variate on args.cv plain samples, then time steps of the chosen form
+    (one batch of paired samples plus cheap samples per step) against the plain estimator on the
+    same paired samples."""
+    import torch
+    from paper_2601_21005_gb300.control_variate import ControlVariate
+    ns = cfg['samples_per_batch']
+    cv = ControlVariate(pl, m2max=10, width=256, max_batch=256, seed=11)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Yt, Ft = cv.collect(args.cv, base + 300000)
+    tr, va = cv.train(Ft, Yt, epochs=200, batch=64, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n_cheap = args.cv_cheap
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ys, Fs = [], []
+    e0.record(st)
+    for b in range(args.cv_paired_batches):
+        Y, F = cv.collect(ns, base + 400000 + b * ns)
+        Ys.append(Y)
+        Fs.append(F)
+    Fc = cv.cheap_features(n_cheap, base + 500000)
+    Yp, Fp = torch.cat(Ys), torch.cat(Fs)
+    S1, X1 = cv.rows(Fc, Fp, Yp)
+    r_cv = pl.qp(S1, X1, ks['e_homo'])
+    e1.record(st)
+    torch.cuda.synchronize()
+    sec = e0.elapsed_time(e1) * 1e-3
+    S0, X0 = cv.plain_rows(Yp)
+    r_pl = pl.qp(S0, X0, ks['e_homo'])
+    n = Yp.shape[0]
+    per_sample_s = sec / n                 # paired samples plus their share of the cheap ones
+    sd_pl, sd_cv = r_pl['se'] * HA_EV * n ** 0.5, r_cv['se'] * HA_EV * n ** 0.5
+    need_pl, need_cv = (sd_pl / 0.03) ** 2, (sd_cv / 0.03) ** 2
+    t_plain = need_pl * per_sample_s
+    t_cv = need_cv * per_sample_s
+    return dict(n_train=args.cv, n_paired=n, n_cheap=n_cheap, train_seconds=round(t_train, 2),
+                heldout_loss_first_best=[round(va[0], 4), round(min(va), 4)] if va else None,
+                qp_eV_plain=round(r_pl['eps_qp'] * HA_EV, 5), se_eV_plain=round(r_pl['se'] * HA_EV, 5),
+                qp_eV_cv=round(r_cv['eps_qp'] * HA_EV, 5), se_eV_cv=round(r_cv['se'] * HA_EV, 5),
+                variance_gain=round((r_pl['se'] / r_cv['se']) ** 2, 3),
+                time_to_0_03eV_plain_s=round(t_plain, 1), time_to_0_03eV_cv_s=round(t_cv, 1),
+                time_to_0_03eV_cv_incl_training_s=round(t_cv + t_train, 1),
+                speedup=round(t_plain / t_cv, 3), speedup_incl_training=round(t_plain / (t_cv + t_train), 3))
 
 
 def main():
@@ -392,6 +471,11 @@ def main():
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--ks-cache', default=None,
                     help='npz file for the Kohn-Sham inputs (read if present, else computed and written)')
+    ap.add_argument('--no-graphs', dest='graphs', action='store_false',
+                    help='launch every kernel directly instead of replaying the loops as CUDA graphs')
+    ap.add_argument('--cv', type=int, default=128, help='control-variate training samples (0: skip the study)')
+    ap.add_argument('--cv-cheap', type=int, default=4096, help='cheap (features-only) samples in the study')
+    ap.add_argument('--cv-paired-batches', type=int, default=8, help='batches of paired samples in the study')
     ap.add_argument('--scale', type=float, default=1.0,
                     help='scale N_tau and N_chb together (profiling captures of fewer launches)')
     args = ap.parse_args()

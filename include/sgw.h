@@ -73,6 +73,17 @@ void sgw_destroy(sgw_ctx* ctx);
 sgw_status sgw_set_stream(sgw_ctx* ctx, void* stream);
 
 /*
+ * Graph mode (enable != 0): sgw_filter_occupied, sgw_propagate, sgw_tdh_response and sgw_sigma_c
+ * capture their whole launch sequence (every Chebyshev term of every time step) into a CUDA graph
+ * on their first call with a given set of arguments and buffers, and replay the instantiated graph
+ * on later calls with the same ones (up to 8 cached graphs per context; the cache is dropped when
+ * the potential, the stream or a work area changes).  Results are identical to direct launches.
+ * Needs a non-default stream; ignored on the default stream and while profiling is enabled.
+ * Such calls must not themselves be made inside a caller's stream capture.
+ */
+sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
+
+/*
  * Set H0 = T + V_loc + V_NL (Eq. 1 with the ionic pseudopotential split into a local
  * part, folded with V_H[rho0] + V_xc into vloc, and Kleinman-Bylander projectors).
  *  vloc_dev: [N_g] float, local potential (copied; the caller may free it afterwards).

@@ -29,7 +29,8 @@ class ControlVariate:
         self.n_sig = 2 * (2 * pipeline.n_steps + 1)
         self.n_out = self.n_sig + 1
         self.max_batch = max_batch
-        self.mlp = _sgw.MLP(self.n_feat, width, self.n_out, max_batch, seed=seed, device=pipeline.dev.index or 0)
+        self.mlp = _sgw.MLP(self.n_feat, width, self.n_out, max_batch, seed=seed, device=pipeline.dev.index or 0,
+                            stream=pipeline.stream.cuda_stream if pipeline.stream is not None else None)
         # X is one output against 2 (2N + 1) for Sigma(t) but carries a comparable share of the
         # QP variance: give it half the weight of the whole Sigma block.
         w = np.ones(self.n_out, dtype=np.float32)
@@ -45,6 +46,10 @@ class ControlVariate:
 
     # -------------------------------------------------------------- data
     def collect(self, n_samples, sample0):
+        with self.pl.on_stream():
+            return self._collect(n_samples, sample0)
+
+    def _collect(self, n_samples, sample0):
         """Plain samples sample0.. : (Y [n][n_out] f64 = [Sigma(t) interleaved, X], F [n][n_feat] f32)."""
         t, pl = self.torch, self.pl
         ns = pl.ns
@@ -54,12 +59,16 @@ class ControlVariate:
         F = t.empty(nb * ns, self.n_feat, dtype=t.float32, device=pl.dev)
         for b in range(nb):
             s0 = b * ns
-            pl.run_batch(sample0 + s0, S[s0:s0 + ns], X[s0:s0 + ns])
+            pl._run_batch(sample0 + s0, S[s0:s0 + ns], X[s0:s0 + ns])
             pl.ctx.cv_features(pl.noise, ns, pl.n_eta + 1, pl.phi, self.m2max, F[s0:s0 + ns])
         Y = t.cat([t.view_as_real(S).reshape(nb * ns, -1), X[:, None]], dim=1)[:n_samples].contiguous()
         return Y, F[:n_samples].contiguous()
 
     def cheap_features(self, n_samples, sample0):
+        with self.pl.on_stream():
+            return self._cheap_features(n_samples, sample0)
+
+    def _cheap_features(self, n_samples, sample0):
         """Features of samples sample0.. from their white noise alone (no filter, no propagation)."""
         t, pl = self.torch, self.pl
         nv = pl.n_eta + 1
@@ -75,6 +84,10 @@ class ControlVariate:
 
     # -------------------------------------------------------------- network
     def train(self, F, Y, epochs=300, batch=64, lr=1e-3, holdout=0.2):
+        with self.pl.on_stream():
+            return self._train(F, Y, epochs, batch, lr, holdout)
+
+    def _train(self, F, Y, epochs, batch, lr, holdout):
         """Standardise and fit; the parameters of the epoch with the lowest held-out loss are kept.
         Returns (training losses, held-out losses)."""
         t, ctx = self.torch, self.pl.ctx
@@ -105,6 +118,10 @@ class ControlVariate:
         return tr_l, va_l
 
     def predict(self, F):
+        with self.pl.on_stream():
+            return self._predict(F)
+
+    def _predict(self, F):
         """Network outputs (standardised units) for raw features F."""
         t = self.torch
         Fs = F.clone()
@@ -117,13 +134,17 @@ class ControlVariate:
 
     # -------------------------------------------------------------- estimator
     def rows(self, F_cheap, F_paired, Y_paired):
+        with self.pl.on_stream():
+            return self._rows(F_cheap, F_paired, Y_paired)
+
+    def _rows(self, F_cheap, F_paired, Y_paired):
         """Control-variate rows: (Sigma rows [n][2N+1] complex128, X rows [n] f64)."""
         t = self.torch
         rows = t.empty_like(Y_paired)
         if F_cheap is None:
             self.pl.ctx.cv_rows(None, None, Y_paired, None, None, rows)
         else:
-            self.pl.ctx.cv_rows(self.predict(F_cheap), self.predict(F_paired), Y_paired, self.mu, self.sd, rows)
+            self.pl.ctx.cv_rows(self._predict(F_cheap), self._predict(F_paired), Y_paired, self.mu, self.sd, rows)
         n = rows.shape[0]
         sig = t.view_as_complex(rows[:, :self.n_sig].contiguous().reshape(n, -1, 2)).contiguous()
         return sig, rows[:, self.n_sig].contiguous()

@@ -51,6 +51,14 @@ struct sgw_ctx {
     double prof_ms[SGW_PROF_KINDS] = {0};
     int64_t prof_n[SGW_PROF_KINDS] = {0};
     double prof_bytes[SGW_PROF_KINDS] = {0};   // algorithmic (compulsory) HBM bytes of the launches
+    // CUDA graphs of whole propagation loops, keyed by the call's arguments and buffers
+    bool graph_mode = false;
+    struct GraphEntry {
+        std::vector<uint64_t> key;
+        cudaGraphExec_t exec;
+        int64_t n_launch;
+    };
+    std::vector<GraphEntry> graphs;
     std::string err;
 };
 
@@ -135,9 +143,15 @@ sgw_status fail(sgw_ctx* c, sgw_status s, const std::string& msg) {
         if (e_ != cudaSuccess) return fail(ctx, SGW_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
     } while (0)
 
+void clear_graphs(sgw_ctx* ctx) {
+    for (auto& g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+}
+
 // Grow work area `slot` to at least `bytes`.
 sgw_status work(sgw_ctx* ctx, int slot, size_t bytes, void** out) {
     if (ctx->work_sz[slot] < bytes) {
+        clear_graphs(ctx);
         if (ctx->work[slot]) {
             cudaStreamSynchronize(ctx->stream);
             cudaFree(ctx->work[slot]);
@@ -349,6 +363,56 @@ sgw_status upload_info(sgw_ctx* ctx, const std::vector<sgw::VecInfo>& v) {
     return SGW_OK;
 }
 
+uint64_t bits(double x) {
+    uint64_t u;
+    std::memcpy(&u, &x, 8);
+    return u;
+}
+
+uint64_t fnv(const void* p, size_t n) {
+    const unsigned char* c = (const unsigned char*)p;
+    uint64_t h = 1469598103934665603ull;
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+// Run `body` (which only enqueues kernels on the context's stream) directly, or -- in graph
+// mode, on a non-default stream, with profiling off -- through a CUDA graph captured on its
+// first call with this key and replayed on later calls.
+template <class F>
+sgw_status graphed(sgw_ctx* ctx, std::vector<uint64_t> key, F&& body) {
+    if (!ctx->graph_mode || ctx->prof || ctx->stream == nullptr) return body();
+    key.push_back(bits(ctx->emin));
+    key.push_back(bits(ctx->emax));
+    for (auto& g : ctx->graphs)
+        if (g.key == key) {
+            CK(cudaGraphLaunch(g.exec, ctx->stream));
+            ctx->launches += g.n_launch;
+            return SGW_OK;
+        }
+    const int64_t l0 = ctx->launches;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    sgw_status s = body();
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (s != SGW_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+    }
+    CK(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    if (ctx->graphs.size() >= 8) {
+        cudaGraphExecDestroy(ctx->graphs.front().exec);
+        ctx->graphs.erase(ctx->graphs.begin());
+    }
+    ctx->graphs.push_back({key, ex, ctx->launches - l0});
+    CK(cudaGraphLaunch(ex, ctx->stream));
+    return SGW_OK;
+}
+
 void prop_coeffs(sgw_ctx* ctx, double dt, int K, std::vector<cd> c[2], cd phase[2]) {
     const double ebar = 0.5 * (ctx->emax + ctx->emin), de = 0.5 * (ctx->emax - ctx->emin);
     const std::vector<double> J = bessel_j(K, de * std::fabs(dt));
@@ -447,12 +511,21 @@ void sgw_destroy(sgw_ctx* ctx) {
             cudaEventDestroy(pr.second);
         }
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    clear_graphs(ctx);
     delete ctx;
 }
 
 sgw_status sgw_set_stream(sgw_ctx* ctx, void* stream) {
     if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    clear_graphs(ctx);
     ctx->stream = (cudaStream_t)stream;
+    return SGW_OK;
+}
+
+sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable) {
+    if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    if (!enable) clear_graphs(ctx);
+    ctx->graph_mode = enable != 0;
     return SGW_OK;
 }
 
@@ -463,6 +536,7 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
     if (s) return s;
     if (!vloc_dev) return fail(ctx, SGW_EINVAL, "vloc_dev is null");
     if (n_atoms < 0) return fail(ctx, SGW_EINVAL, "n_atoms < 0");
+    clear_graphs(ctx);
     CK(cudaMemcpyAsync(ctx->vloc, vloc_dev, sizeof(float) * ctx->ng, cudaMemcpyDeviceToDevice, ctx->stream));
     // drop any previous KB data
     CK(cudaStreamSynchronize(ctx->stream));
@@ -822,8 +896,12 @@ sgw_status sgw_filter_occupied(sgw_ctx* ctx, const double* coeffs_host, int n_ch
     const std::vector<Step> plan = clenshaw_plan(c, one, n_cheb);
     std::vector<sgw::VecInfo> info(batch, sgw::VecInfo{0, -1, -1, 0});
     if ((s = upload_info(ctx, info))) return s;
-    return run_series(ctx, plan, (const float2*)in_dev, (float2*)out_dev, batch, ctx->vloc, nullptr, ctx->info, false,
-                      false);
+    std::vector<uint64_t> key = {1, (uint64_t)n_cheb, (uint64_t)batch, (uint64_t)in_dev, (uint64_t)out_dev,
+                                 fnv(coeffs_host, sizeof(double) * (n_cheb + 1))};
+    return graphed(ctx, key, [&]() {
+        return run_series(ctx, plan, (const float2*)in_dev, (float2*)out_dev, batch, ctx->vloc, nullptr, ctx->info,
+                          false, false);
+    });
 }
 
 sgw_status sgw_white_noise(sgw_ctx* ctx, uint64_t seed, uint32_t stream_id, int sample0, int n_samples, int n_vec,
@@ -874,10 +952,15 @@ sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, do
         }
     if ((s = upload_info(ctx, info))) return s;
     float2* psi = (float2*)psi_dev;
-    for (int j = 0; j < n_steps; ++j) {
-        if ((s = run_series(ctx, plan, psi, psi, batch, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps))) return s;
-    }
-    return SGW_OK;
+    std::vector<uint64_t> key = {2, (uint64_t)batch, (uint64_t)n_steps, bits(dt), (uint64_t)cheb_deg, (uint64_t)psi,
+                                 fnv(info.data(), sizeof(sgw::VecInfo) * info.size())};
+    return graphed(ctx, key, [&]() {
+        for (int j = 0; j < n_steps; ++j) {
+            sgw_status r = run_series(ctx, plan, psi, psi, batch, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps);
+            if (r) return r;
+        }
+        return SGW_OK;
+    });
 }
 
 sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* source_dev, int n_samples, int n_eta,
@@ -905,17 +988,6 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
     float* dv = vtot + ng * n_samples;
     float* rho0 = dv + ng * n_samples;
     float* vp = rho0 + ng * n_samples;
-    // v_p = v_C * source (Poisson, periodic, k = 0 dropped)
-    {
-        Launch L(ctx, SGW_PROF_OTHER, 5);
-        sgw::launch_real_to_c64(ng * n_samples, source_dev, ctx->B1, st);
-        sgw::launch_plane_fwd(n, ctx->B1, Wp, n_samples, ctx->tw, st);
-        sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
-        sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 2, nullptr, nullptr, nullptr, nullptr, nullptr, 0, vp, st);
-        // eta pairs: (eta, d eta = -i v_p eta)
-        sgw::launch_kick((int)ng, (const float2*)eta_dev, vp, n_samples, n_eta, psi, st);
-        CKL();
-    }
     std::vector<sgw::VecInfo> info(B);
     for (int sm = 0; sm < n_samples; ++sm)
         for (int l = 0; l < 2 * n_eta; ++l) {
@@ -929,26 +1001,42 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
     prop_coeffs(ctx, dt, cheb_deg, c, ph);
     const std::vector<Step> plan = clenshaw_plan(c, ph, cheb_deg);
     const int64_t uR_stride = (int64_t)(n_steps + 1) * ng;
-    for (int j = 0; j <= n_steps; ++j) {
-        // H(t_j): density, Poisson of (rho - rho0) + i d rho, potentials and u^R(t_j)
+    std::vector<uint64_t> key = {3, (uint64_t)n_samples, (uint64_t)n_eta, (uint64_t)n_steps, bits(dt),
+                                 (uint64_t)cheb_deg, bits(w), (uint64_t)eta_dev, (uint64_t)source_dev, (uint64_t)uR_dev,
+                                 (uint64_t)psi, (uint64_t)Wp, (uint64_t)vtot};
+    return graphed(ctx, key, [&]() -> sgw_status {
+        // v_p = v_C * source (Poisson, periodic, k = 0 dropped)
         {
-            Launch L(ctx, SGW_PROF_TDH_DENSITY, 1, (double)ctx->ng * (8.0 * 2 * n_eta * n_samples + 12.0 * n_samples));
-            sgw::launch_density_fwd(n, psi, n_samples, n_eta, w, rho0, j == 0 ? 1 : 0, Wp, ctx->tw, st);
-        }
-        {
-            Launch L(ctx, SGW_PROF_OTHER);
+            Launch L(ctx, SGW_PROF_OTHER, 5);
+            sgw::launch_real_to_c64(ng * n_samples, source_dev, ctx->B1, st);
+            sgw::launch_plane_fwd(n, ctx->B1, Wp, n_samples, ctx->tw, st);
             sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+            sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 2, nullptr, nullptr, nullptr, nullptr, nullptr, 0, vp, st);
+            // eta pairs: (eta, d eta = -i v_p eta)
+            sgw::launch_kick((int)ng, (const float2*)eta_dev, vp, n_samples, n_eta, psi, st);
+            CKL();
         }
-        {
-            Launch L(ctx, SGW_PROF_OTHER);
-            sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 1, nullptr, ctx->vloc, vtot, dv,
-                                  uR_dev + (int64_t)j * ng, uR_stride, nullptr, st);
+        for (int j = 0; j <= n_steps; ++j) {
+            // H(t_j): density, Poisson of (rho - rho0) + i d rho, potentials and u^R(t_j)
+            {
+                Launch L(ctx, SGW_PROF_TDH_DENSITY, 1, (double)ctx->ng * (8.0 * 2 * n_eta * n_samples + 12.0 * n_samples));
+                sgw::launch_density_fwd(n, psi, n_samples, n_eta, w, rho0, j == 0 ? 1 : 0, Wp, ctx->tw, st);
+            }
+            {
+                Launch L(ctx, SGW_PROF_OTHER);
+                sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+            }
+            {
+                Launch L(ctx, SGW_PROF_OTHER);
+                sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 1, nullptr, ctx->vloc, vtot, dv,
+                                      uR_dev + (int64_t)j * ng, uR_stride, nullptr, st);
+            }
+            CKL();
+            if (j == n_steps) break;
+            if (sgw_status s2 = run_series(ctx, plan, psi, psi, B, vtot, dv, ctx->info, j > 0, true, n_samples)) return s2;
         }
-        CKL();
-        if (j == n_steps) break;
-        if ((s = run_series(ctx, plan, psi, psi, B, vtot, dv, ctx->info, j > 0, true, n_samples))) return s;
-    }
-    return SGW_OK;
+        return SGW_OK;
+    });
 }
 
 sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_samples, int n_steps) {
@@ -1005,6 +1093,10 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
     if ((s = upload_info(ctx, info))) return s;
     float2* z = (float2*)zeta_dev;
     const int64_t u_ss = (int64_t)(n_steps + 1) * ng;
+    std::vector<uint64_t> key = {4, (uint64_t)n_samples, (uint64_t)n_steps, bits(dt), (uint64_t)cheb_deg,
+                                 (uint64_t)fp64_accum, (uint64_t)zeta_dev, (uint64_t)phi_dev, (uint64_t)u_dev,
+                                 (uint64_t)sigma_dev, (uint64_t)partial};
+    return graphed(ctx, key, [&]() -> sgw_status {
     for (int j = 0; j <= n_steps; ++j) {
         {
             Launch L(ctx, SGW_PROF_SIGMA, 1, (double)ng * n_samples * (8.0 * 3 + 4.0));
@@ -1013,7 +1105,8 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
             CKL();
         }
         if (j == n_steps) break;
-        if ((s = run_series(ctx, plan, z, z, B, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps))) return s;
+        if (sgw_status s2 = run_series(ctx, plan, z, z, B, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps))
+            return s2;
     }
     {
         Launch L(ctx, SGW_PROF_OTHER);
@@ -1021,6 +1114,7 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
         CKL();
     }
     return SGW_OK;
+    });
 }
 
 sgw_status sgw_exchange(sgw_ctx* ctx, const void* eta_dev, const float* phi_dev, int n_samples, int n_eta,

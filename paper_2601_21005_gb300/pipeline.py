@@ -8,6 +8,8 @@ libsgw; torch only allocates the device buffers and streams:
   zeta propagation with Sigma(t) accumulation (Eq. 4, 5) -> ... over batches ... ->
   Sigma(omega) (Eq. 7) and the QP root (Eq. 6) on the sample means.
 """
+import contextlib
+
 import numpy as np
 
 from . import sgw as _sgw
@@ -16,9 +18,14 @@ from . import sgw as _sgw
 class Pipeline:
     def __init__(self, n, h, vloc, kb_atoms, phi, e_homo, e_lumo, n_eta=8, n_steps=200, dt=0.05,
                  cheb_deg=16, n_cheb=128, samples_per_batch=1, seed=1000, stream_id=1, device=0, ecut=0.0,
-                 spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None):
+                 spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None, graphs=False):
         import torch
         self.torch = torch
+        # CUDA graphs need a non-default stream: the pipeline then owns one, and its buffers are
+        # allocated and used on it
+        self.stream = torch.cuda.Stream(device) if (graphs and stream is None) else None
+        if self.stream is not None:
+            stream = self.stream.cuda_stream
         self.n, self.h, self.ng = n, h, n ** 3
         self.n_eta, self.n_steps, self.dt, self.cheb_deg = n_eta, n_steps, dt, cheb_deg
         self.ns = samples_per_batch
@@ -27,6 +34,8 @@ class Pipeline:
         self.dev = torch.device('cuda', device)
         mb = max(self.ns * (n_eta + 1), 2 * self.ns * n_eta, 2 * self.ns)
         self.ctx = _sgw.Context(n, h, ecut=ecut, max_batch=mb, device=device, stream=stream)
+        if graphs:
+            self.ctx.set_graph_mode(True)
         vl = torch.as_tensor(np.asarray(vloc, dtype=np.float32).reshape(-1)).to(self.dev)
         self.ctx.set_potential(vl, kb_atoms)
         if spectrum is None:
@@ -49,6 +58,19 @@ class Pipeline:
         self.uR = torch.empty(ns, N + 1, ng, dtype=f32, device=self.dev)
         self.u = torch.empty(ns, N + 1, ng, dtype=c64, device=self.dev)
 
+    @contextlib.contextmanager
+    def on_stream(self):
+        """Run the enclosed torch and libsgw work on the pipeline's stream, ordered after the
+        caller's pending work and before the caller's later work."""
+        if self.stream is None:
+            yield
+            return
+        cur = self.torch.cuda.current_stream(self.dev)
+        self.stream.wait_stream(cur)
+        with self.torch.cuda.stream(self.stream):
+            yield
+        cur.wait_stream(self.stream)
+
     @property
     def gamma(self):
         """Damping gamma = 3 / (N_tau dt) (Sec. 3: N_tau ~ 3 / (gamma dt))."""
@@ -56,6 +78,10 @@ class Pipeline:
 
     def run_batch(self, sample0, sigma_out, x_out):
         """Samples sample0 .. sample0 + ns - 1; writes Sigma_i(t) [ns][2N+1] (complex128) and X_i [ns]."""
+        with self.on_stream():
+            self._run_batch(sample0, sigma_out, x_out)
+
+    def _run_batch(self, sample0, sigma_out, x_out):
         c, ns, ne, N = self.ctx, self.ns, self.n_eta, self.n_steps
         c.white_noise(self.seed, self.stream_id, sample0, ns, ne + 1, self.noise)
         c.filter_occupied(self.coeffs, self.noise, self.filt)
@@ -78,5 +104,6 @@ class Pipeline:
 
     def qp(self, sigma, x, eps_ks, vxc=0.0, window=2.0, step=1e-3, fp64=None):
         f = self.fp64 if fp64 is None else (1 if fp64 else 0)
-        return self.ctx.qp_energy(sigma.contiguous(), x.contiguous(), sigma.shape[0], self.n_steps, self.dt,
-                                  self.gamma, eps_ks, vxc, window, step, f)
+        with self.on_stream():
+            return self.ctx.qp_energy(sigma.contiguous(), x.contiguous(), sigma.shape[0], self.n_steps, self.dt,
+                                      self.gamma, eps_ks, vxc, window, step, f)

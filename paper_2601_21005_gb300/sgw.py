@@ -34,6 +34,7 @@ _SIGS = {
     'sgw_setup_grid': ([_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_destroy': ([_P], None),
     'sgw_set_stream': ([_P, _P], _c.c_int),
+    'sgw_set_graph_mode': ([_P, _c.c_int], _c.c_int),
     'sgw_set_potential': ([_P, _P, _c.c_int, _P, _P, _P, _P, _P], _c.c_int),
     'sgw_apply_h': ([_P, _P, _P, _c.c_int], _c.c_int),
     'sgw_spectral_bounds': ([_P, _c.c_int, _c.c_uint64, _c.c_double, _P, _P, _P], _c.c_int),
@@ -266,6 +267,9 @@ class Context:
 
     def set_stream(self, stream):
         self._ck('sgw_set_stream', lib().sgw_set_stream(self._p, _P(stream)))
+
+    def set_graph_mode(self, enable):
+        self._ck('sgw_set_graph_mode', lib().sgw_set_graph_mode(self._p, 1 if enable else 0))
 
     def set_potential(self, vloc_dev, kb_atoms=()):
         """kb_atoms: list of (support flat indices, beta [n_proj, n_sup], e [n_proj])."""
