@@ -273,7 +273,7 @@ def run_ours(args, cfg):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group('nccl', device_id=torch.device('cuda', local))
-    from paper_2601_21005_gb300 import build
+    from paper_2601_21005_gb300 import build, replicas
     build.build()
     peaks = load_peaks()
     seed = 1000 * 2
@@ -292,7 +292,7 @@ def run_ours(args, cfg):
     nb_total = args.warmup + args.steps
     sig = torch.empty(nb_total * ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
     xs = torch.empty(nb_total * ns, dtype=torch.float64, device='cuda')
-    base = rank * 1000000          # each rank draws its own samples: no data-path collective
+    base = replicas.sample_base(rank)   # each rank draws its own samples: no data-path collective
     eps_ks = ks['e_homo']
 
     def step(b):
@@ -334,13 +334,12 @@ def run_ours(args, cfg):
     else:
         prof = pl.ctx.profile_read()
         pl.ctx.profile(False)
-    if dist:
-        t = torch.tensor([ms], device='cuda', dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, dist, 'cuda')
     ms_per_step = ms / args.steps
-    value = units_per_step(cfg) * args.steps * world / (ms * 1e-3)
-    tt = time_to_target(pl, sig, xs, eps_ks, ms_per_step * 1e-3 / ns)
+    value = replicas.job_throughput(units_per_step(cfg), args.steps, world, ms)
+    # one QP solve over every rank's samples (gathered after the timed region)
+    sig_all, xs_all = replicas.gather_rows(sig, xs, dist)
+    tt = time_to_target(pl, sig_all, xs_all, eps_ks, ms_per_step * 1e-3 / (ns * world))
 
     # end to end through the public API: per step the target orbital comes from pinned host
     # memory and Sigma(t), X and the QP result go back to the host
@@ -362,11 +361,8 @@ def run_ours(args, cfg):
     e1.record(st)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_e2e], device='cuda', dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = dict(value=units_per_step(cfg) * args.steps * world / (ms_e2e * 1e-3), unit=UNIT,
+    ms_e2e = replicas.max_over_ranks(ms_e2e, dist, 'cuda')
+    e2e = dict(value=replicas.job_throughput(units_per_step(cfg), args.steps, world, ms_e2e), unit=UNIT,
                h2d_bytes_per_step=phi_h.numel() * 4, d2h_bytes_per_step=sig_h.numel() * 16 + x_h.numel() * 8 + 32)
     # plain FP32 form (Sigma reductions, transform and QP in FP32) on the same samples as the
     # mixed form (FP64 there): the eV difference of the QP energy
