@@ -126,12 +126,12 @@ def kohn_sham_inputs(cfg, sysd, device):
                 raw_bounds=raw, eig_residual=res)
 
 
-def make_pipeline(cfg, sysd, ks, device, seed, fp64=True, graphs=False):
+def make_pipeline(cfg, sysd, ks, device, seed, fp64=True, graphs=False, autotune=False):
     from paper_2601_21005_gb300.pipeline import Pipeline
     return Pipeline(cfg['n'], cfg['h'], sysd['vloc'], sysd['kb_atoms'], ks['phi'], ks['e_homo'], ks['e_lumo'],
                     n_eta=cfg['n_eta'], n_steps=cfg['n_steps'], dt=cfg['dt'], cheb_deg=cfg['cheb_deg'],
                     n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'], seed=seed, stream_id=1,
-                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64, graphs=graphs)
+                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64, graphs=graphs, autotune=autotune)
 
 
 def units_per_step(cfg):
@@ -286,7 +286,7 @@ def run_ours(args, cfg):
         ks = kohn_sham_inputs(cfg, sysd, local)
         if args.ks_cache:
             np.savez(args.ks_cache, **{k: np.asarray(v) for k, v in ks.items()})
-    pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs)
+    pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs, autotune=args.autotune)
     t_setup = time.perf_counter() - t_setup
     ns = cfg['samples_per_batch']
     nb_total = args.warmup + args.steps
@@ -381,6 +381,9 @@ def run_ours(args, cfg):
                             samples_per_step=ns * world, l2='inputs larger than L2 (about 5 GB live per batch)',
                             precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world,
                             cuda_graphs=bool(args.graphs),
+                            launch_tuning=dict(zip(('plane_operand_prefetch', 'plane_lookahead', 'pencil_lookahead',
+                                                    'plane_threads_variant'),
+                                                   pl.tuning)) if pl.tuning else 'defaults',
                             roofline_timing='per-kernel CUDA events over the timed region' if not args.graphs else
                             'per-kernel CUDA events over one extra step (graph replay is timed unprofiled)'),
                 e2e=e2e, gpu_launches=int(launches), roofline=rl, cpu_baseline=cpu,
@@ -469,6 +472,8 @@ def main():
                     help='npz file for the Kohn-Sham inputs (read if present, else computed and written)')
     ap.add_argument('--no-graphs', dest='graphs', action='store_false',
                     help='launch every kernel directly instead of replaying the loops as CUDA graphs')
+    ap.add_argument('--no-autotune', dest='autotune', action='store_false',
+                    help='keep the default launch hints instead of timing the candidates at setup')
     ap.add_argument('--cv', type=int, default=128, help='control-variate training samples (0: skip the study)')
     ap.add_argument('--cv-cheap', type=int, default=4096, help='cheap (features-only) samples in the study')
     ap.add_argument('--cv-paired-batches', type=int, default=8, help='batches of paired samples in the study')

@@ -84,6 +84,47 @@ sgw_status sgw_set_stream(sgw_ctx* ctx, void* stream);
 sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
 
 /*
+ * Launch tuning (the paper's GPU port batches all vectors of a step into each launch, Sec. 2.3;
+ * these keys refine how those launches use the memory system).  Every key is a performance hint:
+ * no result depends on it.
+ *   SGW_TUNE_PLANE_OPERANDS   : 1 = each xy-plane pass block starts by prefetching into L2 the
+ *                               operands of its pointwise step (b_{k+1}, psi, b_{k+2}, potential
+ *                               rows), so they arrive while its inverse transform runs; 0 = off
+ *                               (default 1)
+ *   SGW_TUNE_PLANE_LOOKAHEAD  : each xy-plane pass block also prefetches into L2 the input plane of
+ *                               the block this many blocks later in launch order (0 = off, default)
+ *   SGW_TUNE_PENCIL_LOOKAHEAD : the same for the z-pencil pass, in pencil blocks (0 = off, default)
+ *   SGW_TUNE_PLANE_THREADS    : threads per block of the xy-plane pass of a Chebyshev term: 0 = the
+ *                               default shape (n^2/16 for n = 64), 1 = twice as many, one butterfly
+ *                               per thread per FFT stage (default 0)
+ * sgw_set_tuning returns SGW_EINVAL for an unknown key or a negative value (a value above 1 for
+ * SGW_TUNE_PLANE_OPERANDS and SGW_TUNE_PLANE_THREADS) and drops the context's cached graphs; sgw_get_tuning writes the
+ * current value to *value_host.
+ */
+enum {
+    SGW_TUNE_PLANE_OPERANDS = 0,
+    SGW_TUNE_PLANE_LOOKAHEAD = 1,
+    SGW_TUNE_PENCIL_LOOKAHEAD = 2,
+    SGW_TUNE_PLANE_THREADS = 3,
+    SGW_TUNE_KEYS = 4
+};
+sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value);
+sgw_status sgw_get_tuning(sgw_ctx* ctx, int key, int* value_host);
+
+/*
+ * Autotuner: time `reps` degree-8 Chebyshev sums (the propagator's two-pass term, KB included when
+ * a KB part is set) on a scratch batch of `batch` vectors for each candidate value (plane threads
+ * 0/1, then operand prefetch 0/1, then the lookaheads 0 and 1/2, 1, 3/2, 2 waves of resident
+ * blocks from the occupancy of this GPU), keep the fastest per key, each key timed with the
+ * choices already made for the keys before it, and write the chosen values to chosen_host
+ * [SGW_TUNE_KEYS] (may be NULL).  Needs sgw_set_potential and a spectral interval (SGW_ESTATE
+ * otherwise); 1 <= batch <= max_batch and reps >= 1 (SGW_EINVAL otherwise).  Uses a context work
+ * area of 2 batch-sized complex arrays (SGW_ENOMEM if it cannot grow).  Synchronises; must not be
+ * called inside a stream capture.
+ */
+sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host);
+
+/*
  * Set H0 = T + V_loc + V_NL (Eq. 1 with the ionic pseudopotential split into a local
  * part, folded with V_H[rho0] + V_xc into vloc, and Kleinman-Bylander projectors).
  *  vloc_dev: [N_g] float, local potential (copied; the caller may free it afterwards).

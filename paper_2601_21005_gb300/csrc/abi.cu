@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
+#include <initializer_list>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -59,6 +61,8 @@ struct sgw_ctx {
         int64_t n_launch;
     };
     std::vector<GraphEntry> graphs;
+    // launch tuning hints (sgw_set_tuning / sgw_autotune); no result depends on them
+    int tune[SGW_TUNE_KEYS] = {1, 0, 0, 0};
     std::string err;
 };
 
@@ -129,6 +133,15 @@ sgw_status fail(sgw_ctx* c, sgw_status s, const std::string& msg) {
     else g_setup_err = msg;
     return s;
 }
+
+// Device buffers the kernels read or write with 16-byte vector accesses or bulk copies.
+bool misaligned(std::initializer_list<const void*> ps) {
+    for (const void* p : ps)
+        if (reinterpret_cast<uintptr_t>(p) & 15u) return true;
+    return false;
+}
+#define SGW_ALIGNED(ctx, ...) \
+    if (misaligned({__VA_ARGS__})) return fail(ctx, SGW_EINVAL, "device buffers must be 16-byte aligned")
 
 #define CK(call)                                                                                      \
     do {                                                                                              \
@@ -265,6 +278,35 @@ std::vector<Step> clenshaw_plan(const std::vector<cd>* c, const cd* phase, int K
     return plan;
 }
 
+// Free every KB device array of the context
+void free_kb(sgw_ctx* ctx) {
+    sgw::KBDev& kb = ctx->kb;
+    void* ptrs[] = {kb.atom_nproj, kb.atom_off, kb.sup_idx, kb.sup_beta, kb.atom_e, kb.plane_off, kb.slot_atom,
+                    kb.kbe_col, kb.kbe_os, kb.kbe_beta, kb.kbe_slot_beg, kb.kbe_slot_end, kb.atom_pos_off,
+                    kb.atom_pos, ctx->kbc, ctx->kbp};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    kb = sgw::KBDev();
+    ctx->kbc = nullptr;
+    ctx->kbp = nullptr;
+}
+
+// KB table pointers of a plane-step launch
+void set_kb_args(const sgw_ctx* ctx, sgw::StepArgs& a) {
+    const sgw::KBDev& kb = ctx->kb;
+    a.plane_off = kb.plane_off;
+    a.slot_atom = kb.slot_atom;
+    a.kbe_col = kb.kbe_col;
+    a.kbe_os = kb.kbe_os;
+    a.kbe_beta = kb.kbe_beta;
+    a.kbe_slot_beg = kb.kbe_slot_beg;
+    a.kbe_slot_end = kb.kbe_slot_end;
+    a.max_colors = kb.max_colors;
+    a.max_plane_slots = kb.max_plane_slots;
+    a.total_slots = kb.total_slots;
+    a.n_proj = kb.n_proj;
+}
+
 // Run one Chebyshev sum over a batch.  psi_in: real-space input; out: result (may alias psi_in).
 // W must hold the forward xy transform of psi_in on entry when w_ready; on exit it holds the
 // transform of the output when want_wout.
@@ -304,7 +346,8 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
         }
         {
             Launch L(ctx, SGW_PROF_PENCIL, 1, 16.0 * (double)ctx->ng * batch);
-            sgw::launch_pencil(n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, st);
+            sgw::launch_pencil(n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, st,
+                               ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD]);
             CKL();
         }
         sgw::StepArgs a{};
@@ -319,19 +362,14 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
         a.dvpot = dvpot;
         a.info = info;
         a.kbc = ctx->kb.n_atoms > 0 ? ctx->kbc : nullptr;
-        a.pt_ptr = ctx->kb.pt_ptr;
-        a.pt_atom = ctx->kb.pt_atom;
-        a.pt_beta = ctx->kb.pt_beta;
         a.kbp = (ctx->kb.n_atoms > 0 && a.Wout != nullptr) ? ctx->kbp : nullptr;
-        a.sup_idx = ctx->kb.sup_idx;
-        a.sup_beta = ctx->kb.sup_beta;
-        a.slot_beg = ctx->kb.slot_beg;
-        a.slot_end = ctx->kb.slot_end;
-        a.plane_off = ctx->kb.plane_off;
+        set_kb_args(ctx, a);
         a.total_slots = ctx->kb.total_slots;
         a.n_proj = ctx->kb.n_proj;
         a.ebar = (float)ebar;
         a.alpha = (float)(2.0 / de);
+        a.pf_ahead = ctx->tune[SGW_TUNE_PLANE_LOOKAHEAD];
+        a.pf_operands = ctx->tune[SGW_TUNE_PLANE_OPERANDS];
         for (int q = 0; q < 2; ++q) {
             a.coef.cpsi[q] = f2(s.cpsi[q]);
             a.coef.ch[q] = f2(s.ch[q]);
@@ -344,7 +382,7 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
             double bytes = per * (double)ctx->ng * batch + 4.0 * (double)ctx->ng * vrows * (dvpot ? 2 : 1);
             if (a.kbc) bytes += 4.0 * (double)ctx->ng + 20.0 * (double)ctx->kb.n_sup;
             Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
-            sgw::launch_plane_step(n, a, batch, ctx->tw, st);
+            sgw::launch_plane_step(n, a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_PLANE_THREADS]);
             CKL();
         }
     }
@@ -497,10 +535,8 @@ void sgw_destroy(sgw_ctx* ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    void* ptrs[] = {ctx->tw, ctx->vloc, ctx->W, ctx->B1, ctx->B2, ctx->info, ctx->kbc, ctx->scal, ctx->twM,
-                    ctx->kb.atom_nproj, ctx->kb.atom_off, ctx->kb.sup_idx, ctx->kb.sup_beta, ctx->kb.atom_e,
-                    ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta, ctx->kb.slot_beg, ctx->kb.slot_end, ctx->kb.plane_off,
-                    ctx->kb.atom_pos_off, ctx->kb.atom_pos, ctx->kbp};
+    free_kb(ctx);
+    void* ptrs[] = {ctx->tw, ctx->vloc, ctx->W, ctx->B1, ctx->B2, ctx->info, ctx->scal, ctx->twM};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 8; ++i)
@@ -529,6 +565,99 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable) {
     return SGW_OK;
 }
 
+sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value) {
+    if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    if (key < 0 || key >= SGW_TUNE_KEYS) return fail(ctx, SGW_EINVAL, "unknown tuning key");
+    if (value < 0 || ((key == SGW_TUNE_PLANE_OPERANDS || key == SGW_TUNE_PLANE_THREADS) && value > 1))
+        return fail(ctx, SGW_EINVAL, "tuning value out of range");
+    clear_graphs(ctx);
+    ctx->tune[key] = value;
+    return SGW_OK;
+}
+
+sgw_status sgw_get_tuning(sgw_ctx* ctx, int key, int* value_host) {
+    if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    if (key < 0 || key >= SGW_TUNE_KEYS || !value_host) return fail(ctx, SGW_EINVAL, "bad tuning query");
+    *value_host = ctx->tune[key];
+    return SGW_OK;
+}
+
+sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
+    if (batch < 1 || batch > ctx->max_batch || reps < 1) return fail(ctx, SGW_EINVAL, "bad autotune arguments");
+    void* p = nullptr;
+    if ((s = work(ctx, 1, sizeof(float2) * ctx->ng * batch * 2, &p))) return s;
+    float2* psi = (float2*)p;
+    float2* out = psi + ctx->ng * batch;
+    clear_graphs(ctx);
+    std::vector<sgw::VecInfo> info(batch, sgw::VecInfo{0, -1, -1, 0});
+    if ((s = upload_info(ctx, info))) return s;
+    {
+        Launch L(ctx, SGW_PROF_OTHER);
+        sgw::launch_noise((int)ctx->ng, 0x7u, 0xA7u, 0, 1, batch, (float)(1.0 / std::sqrt(ctx->dV)), psi, ctx->stream);
+        CKL();
+    }
+    std::vector<cd> c[2];
+    cd ph[2];
+    prop_coeffs(ctx, 0.05, 8, c, ph);
+    const std::vector<Step> plan = clenshaw_plan(c, ph, 8);
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto timed = [&](float* best_ms) -> sgw_status {
+        *best_ms = 1e30f;
+        for (int r = 0; r <= reps; ++r) {          // the first run warms up
+            cudaEventRecord(e0, ctx->stream);
+            sgw_status q = run_series(ctx, plan, psi, out, batch, ctx->vloc, nullptr, ctx->info, false, false);
+            if (q) return q;
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return fail(ctx, SGW_ECUDA, "autotune timing failed");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (r > 0 && ms < *best_ms) *best_ms = ms;
+        }
+        return SGW_OK;
+    };
+    const int order[SGW_TUNE_KEYS] = {SGW_TUNE_PLANE_THREADS, SGW_TUNE_PLANE_OPERANDS, SGW_TUNE_PLANE_LOOKAHEAD,
+                                      SGW_TUNE_PENCIL_LOOKAHEAD};
+    for (int ki = 0; ki < SGW_TUNE_KEYS && !s; ++ki) {
+        const int key = order[ki];
+        std::vector<int> cand = {0, 1};
+        if (key == SGW_TUNE_PLANE_LOOKAHEAD || key == SGW_TUNE_PENCIL_LOOKAHEAD) {
+            const int per_sm = key == SGW_TUNE_PLANE_LOOKAHEAD
+                                   ? sgw::plane_step_blocks_per_sm(ctx->n, ctx->tune[SGW_TUNE_PLANE_THREADS], ctx->kb.max_plane_slots)
+                                   : sgw::pencil_blocks_per_sm(ctx->n);
+            const int R = per_sm * nsm;
+            cand = {0, R / 2, R, (3 * R) / 2, 2 * R};
+        }
+        int best_v = 0;
+        float best = 1e30f;
+        for (int v : cand) {
+            ctx->tune[key] = v;
+            float ms = 0.f;
+            if ((s = timed(&ms))) break;
+            if (ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        ctx->tune[key] = best_v;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->prof = prof;
+    if (s) return s;
+    if (chosen_host)
+        for (int k = 0; k < SGW_TUNE_KEYS; ++k) chosen_host[k] = ctx->tune[k];
+    return SGW_OK;
+}
+
 sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, const int* nproj_host,
                              const int64_t* sup_off_host, const int* sup_idx_host, const float* beta_host,
                              const float* e_host) {
@@ -540,14 +669,7 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
     CK(cudaMemcpyAsync(ctx->vloc, vloc_dev, sizeof(float) * ctx->ng, cudaMemcpyDeviceToDevice, ctx->stream));
     // drop any previous KB data
     CK(cudaStreamSynchronize(ctx->stream));
-    void* old[] = {ctx->kb.atom_nproj, ctx->kb.atom_off, ctx->kb.sup_idx, ctx->kb.sup_beta, ctx->kb.atom_e,
-                   ctx->kb.pt_ptr, ctx->kb.pt_atom, ctx->kb.pt_beta, ctx->kbc, ctx->kb.slot_beg, ctx->kb.slot_end, ctx->kb.plane_off,
-                   ctx->kb.atom_pos_off, ctx->kb.atom_pos, ctx->kbp};
-    for (void* p : old)
-        if (p) cudaFree(p);
-    ctx->kb = sgw::KBDev();
-    ctx->kbc = nullptr;
-    ctx->kbp = nullptr;
+    free_kb(ctx);
     if (n_atoms > 0) {
         if (!nproj_host || !sup_off_host || !sup_idx_host || !beta_host || !e_host)
             return fail(ctx, SGW_EINVAL, "KB arrays must be non-null when n_atoms > 0");
@@ -560,13 +682,11 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
         if (nsup > INT32_MAX) return fail(ctx, SGW_EINVAL, "too many support points");
         for (int64_t i = 0; i < nsup; ++i)
             if (sup_idx_host[i] < 0 || sup_idx_host[i] >= ctx->ng) return fail(ctx, SGW_EINVAL, "support index out of range");
-        // point-major CSR (counting sort by grid index)
-        std::vector<int> cnt(ctx->ng + 1, 0);
-        for (int64_t i = 0; i < nsup; ++i) cnt[sup_idx_host[i] + 1]++;
-        for (int64_t g = 0; g < ctx->ng; ++g) cnt[g + 1] += cnt[g];
-        std::vector<int> pos(cnt.begin(), cnt.end() - 1);
-        std::vector<int> pt_atom(nsup);
-        std::vector<float4> pt_beta(nsup), sup_beta(nsup), atom_e(n_atoms);
+        for (int a = 0; a < n_atoms; ++a)
+            for (int64_t i = sup_off_host[a] + 1; i < sup_off_host[a + 1]; ++i)
+                if (sup_idx_host[i] <= sup_idx_host[i - 1])
+                    return fail(ctx, SGW_EINVAL, "each atom's support indices must be strictly increasing");
+        std::vector<float4> sup_beta(std::max<int64_t>(nsup, 1)), atom_e(n_atoms);
         for (int a = 0; a < n_atoms; ++a) {
             atom_e[a] = make_float4(e_host[4 * a], e_host[4 * a + 1], e_host[4 * a + 2], e_host[4 * a + 3]);
             for (int64_t i = sup_off_host[a]; i < sup_off_host[a + 1]; ++i) {
@@ -575,20 +695,24 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
                 if (nproj_host[a] < 3) b.z = 0.f;
                 if (nproj_host[a] < 2) b.y = 0.f;
                 sup_beta[i] = b;
-                const int p = pos[sup_idx_host[i]]++;
-                pt_atom[p] = a;
-                pt_beta[p] = b;
             }
         }
-        // per-plane slots: one per (plane, atom) pair where the atom's support meets the plane
+        // slots: one per (plane, atom) pair where the atom's support meets the plane; atom a's
+        // points in plane z are one contiguous run of its sorted support: [run_beg, run_end)
         const int n = ctx->n;
         const int64_t plane_sz = (int64_t)n * n;
         std::vector<std::vector<int>> plane_atoms(n);
+        std::vector<std::vector<std::pair<int64_t, int64_t>>> plane_runs(n);
         for (int a = 0; a < n_atoms; ++a) {
-            std::vector<char> hit(n, 0);
-            for (int64_t i = sup_off_host[a]; i < sup_off_host[a + 1]; ++i) hit[sup_idx_host[i] / plane_sz] = 1;
-            for (int z = 0; z < n; ++z)
-                if (hit[z]) plane_atoms[z].push_back(a);
+            int64_t i = sup_off_host[a];
+            while (i < sup_off_host[a + 1]) {
+                const int z = (int)(sup_idx_host[i] / plane_sz);
+                int64_t j = i;
+                while (j < sup_off_host[a + 1] && sup_idx_host[j] / plane_sz == z) ++j;
+                plane_atoms[z].push_back(a);
+                plane_runs[z].push_back({i, j});
+                i = j;
+            }
         }
         std::vector<int> plane_off(n + 1, 0);
         int max_slots = 0;
@@ -597,51 +721,93 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
             max_slots = std::max(max_slots, (int)plane_atoms[z].size());
         }
         const int total_slots = plane_off[n];
+        if (max_slots >= 65536) return fail(ctx, SGW_EINVAL, "too many projector supports meet one plane");
+        const size_t smem = sgw::plane_step_smem(n, max_slots);
+        int optin = 0;
+        CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        if (smem > (size_t)optin)
+            return fail(ctx, SGW_EINVAL, "the projector slots of one plane do not fit in shared memory");
+        CK(sgw::plane_step_reserve_smem(n, smem));
+        std::vector<int> slot_atom(std::max(total_slots, 1));
         std::vector<std::vector<int>> atom_slots(n_atoms);
-        std::vector<std::vector<int>> slot_of(n);   // slot_of[z][k] = atom of local slot k
         for (int z = 0; z < n; ++z)
-            for (int k = 0; k < (int)plane_atoms[z].size(); ++k) atom_slots[plane_atoms[z][k]].push_back(plane_off[z] + k);
+            for (int k = 0; k < (int)plane_atoms[z].size(); ++k) {
+                slot_atom[plane_off[z] + k] = plane_atoms[z][k];
+                atom_slots[plane_atoms[z][k]].push_back(plane_off[z] + k);
+            }
         std::vector<int> atom_pos_off(n_atoms + 1, 0), atom_pos;
         for (int a = 0; a < n_atoms; ++a) {
             atom_pos_off[a + 1] = atom_pos_off[a] + (int)atom_slots[a].size();
             atom_pos.insert(atom_pos.end(), atom_slots[a].begin(), atom_slots[a].end());
         }
-        // support range of each slot: atom a's entries in plane z are contiguous (sorted support)
-        std::vector<int> slot_beg(std::max(total_slots, 1)), slot_end(std::max(total_slots, 1));
-        for (int a = 0; a < n_atoms; ++a) {
-            for (int64_t i = sup_off_host[a]; i < sup_off_host[a + 1]; ++i) {
-                if (i > sup_off_host[a] && sup_idx_host[i] <= sup_idx_host[i - 1])
-                    return fail(ctx, SGW_EINVAL, "each atom's support indices must be strictly increasing");
+        // colour the slots of each plane greedily (lowest colour not used by an overlapping slot)
+        std::vector<int> slot_col(std::max(total_slots, 1), 0);
+        int max_colors = 0;
+        std::vector<uint32_t> mask(plane_sz);
+        for (int z = 0; z < n; ++z) {
+            std::fill(mask.begin(), mask.end(), 0u);
+            for (int k = 0; k < (int)plane_atoms[z].size(); ++k) {
+                uint32_t used = 0;
+                for (int64_t i = plane_runs[z][k].first; i < plane_runs[z][k].second; ++i)
+                    used |= mask[sup_idx_host[i] - z * plane_sz];
+                int c = 0;
+                while (c < 32 && (used >> c & 1u)) ++c;
+                if (c == 32) return fail(ctx, SGW_EINVAL, "more than 32 projector supports overlap at a point");
+                for (int64_t i = plane_runs[z][k].first; i < plane_runs[z][k].second; ++i)
+                    mask[sup_idx_host[i] - z * plane_sz] |= 1u << c;
+                slot_col[plane_off[z] + k] = c;
+                max_colors = std::max(max_colors, c + 1);
             }
-            int q = atom_pos_off[a];
-            int64_t i = sup_off_host[a];
-            while (i < sup_off_host[a + 1]) {
-                const int z = (int)(sup_idx_host[i] / plane_sz);
-                int64_t j = i;
-                while (j < sup_off_host[a + 1] && sup_idx_host[j] / plane_sz == z) ++j;
-                slot_beg[atom_pos[q]] = (int)i;
-                slot_end[atom_pos[q]] = (int)j;
-                ++q;
-                i = j;
+        }
+        // plane-major, colour-major, slot-major entry table
+        std::vector<int> kbe_col((size_t)n * (max_colors + 1), 0);
+        std::vector<unsigned> kbe_os;
+        std::vector<float4> kbe_beta;
+        kbe_os.reserve(nsup);
+        kbe_beta.reserve(nsup);
+        std::vector<int> kbe_slot_beg(std::max(total_slots, 1)), kbe_slot_end(std::max(total_slots, 1));
+        for (int z = 0; z < n; ++z) {
+            for (int c = 0; c < max_colors; ++c) {
+                kbe_col[(size_t)z * (max_colors + 1) + c] = (int)kbe_os.size();
+                for (int k = 0; k < (int)plane_atoms[z].size(); ++k) {
+                    if (slot_col[plane_off[z] + k] != c) continue;
+                    kbe_slot_beg[plane_off[z] + k] = (int)kbe_os.size();
+                    for (int64_t i = plane_runs[z][k].first; i < plane_runs[z][k].second; ++i) {
+                        kbe_os.push_back((unsigned)(sup_idx_host[i] - z * plane_sz) | ((unsigned)k << 16));
+                        kbe_beta.push_back(sup_beta[i]);
+                    }
+                    kbe_slot_end[plane_off[z] + k] = (int)kbe_os.size();
+                }
             }
+            kbe_col[(size_t)z * (max_colors + 1) + max_colors] = (int)kbe_os.size();
         }
         sgw::KBDev& kb = ctx->kb;
         kb.total_slots = total_slots;
         kb.max_plane_slots = max_slots;
+        kb.max_colors = max_colors;
         kb.n_atoms = n_atoms;
         kb.n_proj = 4 * n_atoms;
         kb.n_sup = nsup;
+        const size_t ns1 = std::max<int64_t>(nsup, 1), ts1 = std::max(total_slots, 1);
         bool ok = cudaMalloc(&kb.atom_nproj, sizeof(int) * n_atoms) == cudaSuccess &&
                   cudaMalloc(&kb.atom_off, sizeof(int64_t) * (n_atoms + 1)) == cudaSuccess &&
-                  cudaMalloc(&kb.sup_idx, sizeof(int) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
-                  cudaMalloc(&kb.sup_beta, sizeof(float4) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.sup_idx, sizeof(int) * ns1) == cudaSuccess &&
+                  cudaMalloc(&kb.sup_beta, sizeof(float4) * ns1) == cudaSuccess &&
                   cudaMalloc(&kb.atom_e, sizeof(float4) * n_atoms) == cudaSuccess &&
-                  cudaMalloc(&kb.pt_ptr, sizeof(int) * (ctx->ng + 1)) == cudaSuccess &&
-                  cudaMalloc(&kb.pt_atom, sizeof(int) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
-                  cudaMalloc(&kb.pt_beta, sizeof(float4) * std::max<int64_t>(nsup, 1)) == cudaSuccess &&
-                  cudaMalloc(&ctx->kbc, sizeof(float2) * (size_t)kb.n_proj * ctx->max_batch) == cudaSuccess;
+                  cudaMalloc(&kb.plane_off, sizeof(int) * (n + 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.slot_atom, sizeof(int) * ts1) == cudaSuccess &&
+                  cudaMalloc(&kb.kbe_col, sizeof(int) * kbe_col.size()) == cudaSuccess &&
+                  cudaMalloc(&kb.kbe_os, sizeof(unsigned) * ns1) == cudaSuccess &&
+                  cudaMalloc(&kb.kbe_beta, sizeof(float4) * ns1) == cudaSuccess &&
+                  cudaMalloc(&kb.kbe_slot_beg, sizeof(int) * ts1) == cudaSuccess &&
+                  cudaMalloc(&kb.kbe_slot_end, sizeof(int) * ts1) == cudaSuccess &&
+                  cudaMalloc(&kb.atom_pos_off, sizeof(int) * (n_atoms + 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.atom_pos, sizeof(int) * ts1) == cudaSuccess &&
+                  cudaMalloc(&ctx->kbc, sizeof(float2) * (size_t)kb.n_proj * ctx->max_batch) == cudaSuccess &&
+                  cudaMalloc(&ctx->kbp, sizeof(float2) * 4 * ts1 * ctx->max_batch) == cudaSuccess;
         if (!ok) {
             cudaGetLastError();
+            free_kb(ctx);
             return fail(ctx, SGW_ENOMEM, "KB device allocation failed");
         }
         CK(cudaMemcpy(kb.atom_nproj, nproj_host, sizeof(int) * n_atoms, cudaMemcpyHostToDevice));
@@ -649,22 +815,13 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
         CK(cudaMemcpy(kb.sup_idx, sup_idx_host, sizeof(int) * nsup, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.sup_beta, sup_beta.data(), sizeof(float4) * nsup, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.atom_e, atom_e.data(), sizeof(float4) * n_atoms, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(kb.pt_ptr, cnt.data(), sizeof(int) * (ctx->ng + 1), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(kb.pt_atom, pt_atom.data(), sizeof(int) * nsup, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(kb.pt_beta, pt_beta.data(), sizeof(float4) * nsup, cudaMemcpyHostToDevice));
-        ok = cudaMalloc(&kb.slot_beg, sizeof(int) * std::max(total_slots, 1)) == cudaSuccess &&
-             cudaMalloc(&kb.slot_end, sizeof(int) * std::max(total_slots, 1)) == cudaSuccess &&
-             cudaMalloc(&kb.plane_off, sizeof(int) * (n + 1)) == cudaSuccess &&
-             cudaMalloc(&kb.atom_pos_off, sizeof(int) * (n_atoms + 1)) == cudaSuccess &&
-             cudaMalloc(&kb.atom_pos, sizeof(int) * std::max(total_slots, 1)) == cudaSuccess &&
-             cudaMalloc(&ctx->kbp, sizeof(float2) * 4 * (size_t)std::max(total_slots, 1) * ctx->max_batch) == cudaSuccess;
-        if (!ok) {
-            cudaGetLastError();
-            return fail(ctx, SGW_ENOMEM, "KB device allocation failed");
-        }
-        CK(cudaMemcpy(kb.slot_beg, slot_beg.data(), sizeof(int) * std::max(total_slots, 1), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(kb.slot_end, slot_end.data(), sizeof(int) * std::max(total_slots, 1), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.plane_off, plane_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.slot_atom, slot_atom.data(), sizeof(int) * ts1, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.kbe_col, kbe_col.data(), sizeof(int) * kbe_col.size(), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.kbe_os, kbe_os.data(), sizeof(unsigned) * nsup, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.kbe_beta, kbe_beta.data(), sizeof(float4) * nsup, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.kbe_slot_beg, kbe_slot_beg.data(), sizeof(int) * ts1, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.kbe_slot_end, kbe_slot_end.data(), sizeof(int) * ts1, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.atom_pos_off, atom_pos_off.data(), sizeof(int) * (n_atoms + 1), cudaMemcpyHostToDevice));
         if (total_slots > 0)
             CK(cudaMemcpy(kb.atom_pos, atom_pos.data(), sizeof(int) * total_slots, cudaMemcpyHostToDevice));
@@ -679,6 +836,7 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     if (batch < 0 || batch > ctx->max_batch) return fail(ctx, SGW_EINVAL, "batch out of range");
     if (batch == 0) return SGW_OK;
     if (!in_dev || !out_dev || in_dev == out_dev) return fail(ctx, SGW_EINVAL, "bad in/out pointers");
+    SGW_ALIGNED(ctx, in_dev, out_dev);
     std::vector<sgw::VecInfo> info(batch, sgw::VecInfo{0, -1, -1, 0});
     if ((s = upload_info(ctx, info))) return s;
     const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
@@ -695,7 +853,8 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     }
     {
         Launch L(ctx, SGW_PROF_PENCIL);
-        sgw::launch_pencil(ctx->n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, ctx->stream);
+        sgw::launch_pencil(ctx->n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, ctx->stream,
+                           ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD]);
         CKL();
     }
     sgw::StepArgs a{};
@@ -706,12 +865,13 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     a.vpot = ctx->vloc;
     a.info = ctx->info;
     a.kbc = ctx->kb.n_atoms > 0 ? ctx->kbc : nullptr;
-    a.pt_ptr = ctx->kb.pt_ptr;
-    a.pt_atom = ctx->kb.pt_atom;
-    a.pt_beta = ctx->kb.pt_beta;
+    set_kb_args(ctx, a);
+    a.kbp = nullptr;
     a.n_proj = ctx->kb.n_proj;
     a.ebar = 0.f;
     a.alpha = 1.f;
+    a.pf_ahead = ctx->tune[SGW_TUNE_PLANE_LOOKAHEAD];
+    a.pf_operands = ctx->tune[SGW_TUNE_PLANE_OPERANDS];
     for (int q = 0; q < 2; ++q) {
         a.coef.cpsi[q] = make_float2(0.f, 0.f);
         a.coef.ch[q] = make_float2(1.f, 0.f);
@@ -719,7 +879,7 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     }
     {
         Launch L(ctx, SGW_PROF_PLANE_STEP);
-        sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream);
+        sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream, ctx->tune[SGW_TUNE_PLANE_THREADS]);
         CKL();
     }
     return SGW_OK;
@@ -883,6 +1043,7 @@ sgw_status sgw_filter_occupied(sgw_ctx* ctx, const double* coeffs_host, int n_ch
     if (!coeffs_host || n_cheb < 0 || batch < 0 || batch > ctx->max_batch || !in_dev || !out_dev)
         return fail(ctx, SGW_EINVAL, "bad filter arguments");
     if (batch == 0) return SGW_OK;
+    SGW_ALIGNED(ctx, in_dev, out_dev);
     std::vector<cd> c[2];
     c[0].assign(coeffs_host, coeffs_host + n_cheb + 1);
     c[1] = c[0];
@@ -925,6 +1086,7 @@ sgw_status sgw_prepare_sample(sgw_ctx* ctx, const void* noise_dev, const void* f
     if (n_samples == 0) return SGW_OK;
     if (!noise_dev || !filt_dev || !phi_dev || !eta_dev || !zeta_dev || !source_dev)
         return fail(ctx, SGW_EINVAL, "null prepare pointers");
+    SGW_ALIGNED(ctx, noise_dev, filt_dev, phi_dev, eta_dev, zeta_dev, source_dev);
     Launch L(ctx, SGW_PROF_OTHER);
     sgw::launch_prepare((int)ctx->ng, (const float2*)noise_dev, (const float2*)filt_dev, phi_dev, n_samples, n_eta,
                         (float2*)eta_dev, (float2*)zeta_dev, source_dev, ctx->stream);
@@ -940,6 +1102,7 @@ sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, do
     if (batch < 0 || batch > ctx->max_batch || n_steps < 0 || cheb_deg < 1 || (!psi_dev && batch > 0))
         return fail(ctx, SGW_EINVAL, "bad propagate arguments");
     if (batch == 0 || n_steps == 0) return SGW_OK;
+    SGW_ALIGNED(ctx, psi_dev);
     std::vector<cd> c[2];
     cd ph[2];
     prop_coeffs(ctx, dt, cheb_deg, c, ph);
@@ -972,6 +1135,7 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
         return fail(ctx, SGW_EINVAL, "bad TDH arguments (2 n_samples n_eta must be <= max_batch)");
     if (n_samples == 0) return SGW_OK;
     if (!eta_dev || !source_dev || !uR_dev) return fail(ctx, SGW_EINVAL, "null TDH pointers");
+    SGW_ALIGNED(ctx, eta_dev, source_dev, uR_dev);
     cudaStream_t st = ctx->stream;
     const int n = ctx->n;
     const int64_t ng = ctx->ng;
@@ -1045,6 +1209,7 @@ sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_
     if (n_samples < 0 || n_steps < 0) return fail(ctx, SGW_EINVAL, "bad time-order arguments");
     if (n_samples == 0) return SGW_OK;
     if (!uR_dev || !u_dev) return fail(ctx, SGW_EINVAL, "null time-order pointers");
+    SGW_ALIGNED(ctx, uR_dev, u_dev);
     int M = 64;
     while (M < 4 * (n_steps + 1)) M *= 2;
     if (M > 4096) return fail(ctx, SGW_EINVAL, "n_steps too large for the time-ordering FFT (M <= 4096)");
@@ -1074,6 +1239,7 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
         return fail(ctx, SGW_EINVAL, "bad sigma arguments (2 n_samples must be <= max_batch)");
     if (n_samples == 0) return SGW_OK;
     if (!zeta_dev || !phi_dev || !u_dev || !sigma_dev) return fail(ctx, SGW_EINVAL, "null sigma pointers");
+    SGW_ALIGNED(ctx, zeta_dev, phi_dev, u_dev, sigma_dev);
     cudaStream_t st = ctx->stream;
     const int64_t ng = ctx->ng;
     const int B = 2 * n_samples;
@@ -1124,6 +1290,7 @@ sgw_status sgw_exchange(sgw_ctx* ctx, const void* eta_dev, const float* phi_dev,
     if (n_samples < 0 || n_eta < 1 || n_eta > ctx->max_batch) return fail(ctx, SGW_EINVAL, "bad exchange arguments");
     if (n_samples == 0) return SGW_OK;
     if (!eta_dev || !phi_dev || !x_dev) return fail(ctx, SGW_EINVAL, "null exchange pointers");
+    SGW_ALIGNED(ctx, eta_dev, phi_dev);
     cudaStream_t st = ctx->stream;
     const int64_t ng = ctx->ng;
     const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
@@ -1211,6 +1378,7 @@ sgw_status sgw_cv_features(sgw_ctx* ctx, const void* noise_dev, int n_samples, i
     if (n_samples < 0 || n_vec < 1 || m2max < 1) return fail(ctx, SGW_EINVAL, "bad feature arguments");
     if (n_samples == 0) return SGW_OK;
     if (!noise_dev || !phi_dev || !feat_dev) return fail(ctx, SGW_EINVAL, "null feature pointers");
+    SGW_ALIGNED(ctx, noise_dev, phi_dev);
     const std::vector<int4> ks = cv_kset(m2max);
     const int nk = (int)ks.size();
     const int chunk = std::max(1, ctx->max_batch / n_vec);

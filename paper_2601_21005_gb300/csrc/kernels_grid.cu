@@ -22,11 +22,25 @@ template <int N> struct Cfg {
     // CTAs per SM the plane kernels are compiled for (register budget 65536 / (NT * MINB))
     static constexpr int PLANE_MINB = N == 128 ? 1 : (N == 64 ? 4 : 6);
     static constexpr size_t PENCIL_SMEM = sizeof(float2) * N * TX;
+    // alternative thread count of the fused plane step (one butterfly per thread per stage at 64^2)
+    static constexpr int PLANE_NT2 = 2 * PLANE_NT;
+};
+
+// CTAs per SM the fused plane step is compiled for, by thread count: registers 65536 / (NT MINB)
+template <int N, int NT> struct PlaneMinB {
+    static constexpr int v = 1024 / NT;
+    static constexpr int value = N == 128 ? 1 : (v > 6 ? 6 : (v < 1 ? 1 : v));
 };
 
 __device__ __forceinline__ int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
 
 __device__ __forceinline__ float4 ld4(const float2* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+// Bulk prefetch of `bytes` (multiple of 16) at a 16-byte aligned global address into L2; no data
+// reaches the SM, the later loads of the same lines hit L2.
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void st4(float2* p, float2 a, float2 b) {
     *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
@@ -125,7 +139,7 @@ __device__ __forceinline__ void pencil_forward(const float2* __restrict__ base, 
 
 template <int N, int KIND>
 __global__ void __launch_bounds__(Cfg<N>::PENCIL_NT)
-k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restrict__ tw) {
+k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restrict__ tw, int pf_ahead) {
     extern __shared__ float2 sm[];
     constexpr int NT = Cfg<N>::PENCIL_NT, TX = Cfg<N>::TX, NXT = N / TX;
     constexpr int R1 = ZPlan<N>::R1, R2 = ZPlan<N>::R2, R3 = ZPlan<N>::R3;
@@ -134,6 +148,15 @@ k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restr
     constexpr int PL = (TX * NBL + NT - 1) / NT;
     const int xt = blockIdx.x % NXT, ky = blockIdx.x / NXT;
     float2* base = W + (size_t)blockIdx.y * N * N * N + (size_t)ky * N + xt * TX;
+    if (pf_ahead > 0) {
+        // the N rows (TX points each) of the block pf_ahead later in launch order, into L2
+        const long nxt = (long)blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
+        if (nxt < (long)gridDim.y * gridDim.x && threadIdx.x < N) {
+            const int bx = (int)(nxt % gridDim.x), by = (int)(nxt / gridDim.x);
+            const float2* nb = W + (size_t)by * N * N * N + (size_t)(bx / NXT) * N + (bx % NXT) * TX;
+            l2_prefetch(nb + (size_t)threadIdx.x * N * N, TX * sizeof(float2));
+        }
+    }
     float2 c[PL][RL];
     pencil_forward<N, NT, PL, RL>(base, sm, c, tw);
     // k-space multiply on X[l][kz = j + q NBL]
@@ -212,25 +235,68 @@ k_pencil_energy(const float2* __restrict__ W, int per, float kscale, double dvn,
 }
 
 // ------------------------------------------------------------------ fused Chebyshev step
-template <int N>
-__global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
+template <int N, int NT>
+__global__ void __launch_bounds__(NT, (PlaneMinB<N, NT>::value))
 k_plane_step(StepArgs a, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
-    constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    constexpr int P = N + 1;
     constexpr size_t NG = (size_t)N * N * N;
     const int z = blockIdx.x, b = blockIdx.y;
     const size_t plane = ((size_t)b * N + z) * N * N;
     const VecInfo inf = a.info[b];
-    load_plane<N, NT>(sm, a.W + plane);
-    __syncthreads();
-    fft2_plane<N, NT, +1>(sm, tw);
-
-    const float2 cpsi = a.coef.cpsi[inf.cset], ch = a.coef.ch[inf.cset], c2 = a.coef.c2[inf.cset];
     const float* V = a.vpot + (size_t)inf.vrow * NG + (size_t)z * N * N;
     const float* dV = (a.dvpot != nullptr && inf.dvrow >= 0) ? a.dvpot + (size_t)inf.dvrow * NG + (size_t)z * N * N
                                                                  : nullptr;
     const float2* bp = (dV != nullptr) ? a.b1 + ((size_t)inf.partner * N + z) * N * N : nullptr;
+    if (threadIdx.x == 0 && a.pf_operands) {
+        // the pointwise operands stream into L2 while the inverse transform runs
+        constexpr unsigned PB = N * N * sizeof(float2), VB = N * N * sizeof(float);
+        l2_prefetch(a.b1 + plane, PB);
+        if (a.psi != nullptr) l2_prefetch(a.psi + plane, PB);
+        if (a.b2 != nullptr) l2_prefetch(a.b2 + plane, PB);
+        l2_prefetch(V, VB);
+        if (dV != nullptr) {
+            l2_prefetch(dV, VB);
+            l2_prefetch(bp, PB);
+        }
+    }
+    if (threadIdx.x == 0 && a.pf_ahead > 0) {
+        const long nxt = (long)b * N + z + a.pf_ahead;         // linear id of a later block
+        if (nxt < (long)gridDim.y * N) l2_prefetch(a.W + (size_t)nxt * N * N, N * N * sizeof(float2));
+    }
+    // E-weighted projections of b_{k+1} for the atoms of this plane's slots: kcs[slot][4]
+    float2* kcs = sm + N * P;
     const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
+    const int s0 = kc != nullptr ? __ldg(a.plane_off + z) : 0;
+    if (kc != nullptr) {
+        const int ns = __ldg(a.plane_off + z + 1) - s0;
+        for (int i = threadIdx.x; i < 4 * ns; i += NT) kcs[i] = kc[__ldg(a.slot_atom + s0 + i / 4) * 4 + (i & 3)];
+    }
+    load_plane<N, NT>(sm, a.W + plane);
+    __syncthreads();
+    fft2_plane<N, NT, +1>(sm, tw);
+    if (kc != nullptr) {
+        // KB apply, colour by colour: within a colour every point occurs once, so the adds need no
+        // atomics and their order at a point (colour order) is fixed
+        const int* col = a.kbe_col + z * (a.max_colors + 1);
+        for (int c = 0; c < a.max_colors; ++c) {
+            const int e0 = __ldg(col + c), e1 = __ldg(col + c + 1);
+            if (e0 == e1) break;                  // a plane's colours are used from 0 upwards
+            for (int e = e0 + threadIdx.x; e < e1; e += NT) {
+                const unsigned os = __ldg(a.kbe_os + e);
+                const float4 be = __ldg(a.kbe_beta + e);
+                const int o = (int)(os & 0xffffu), sl = (int)(os >> 16);
+                const float4 c01 = *reinterpret_cast<const float4*>(kcs + 4 * sl);
+                const float4 c23 = *reinterpret_cast<const float4*>(kcs + 4 * sl + 2);
+                float2& hv = sm[(o / N) * P + (o % N)];
+                hv.x += be.x * c01.x + be.y * c01.z + be.z * c23.x + be.w * c23.z;
+                hv.y += be.x * c01.y + be.y * c01.w + be.z * c23.y + be.w * c23.w;
+            }
+            __syncthreads();
+        }
+    }
+
+    const float2 cpsi = a.coef.cpsi[inf.cset], ch = a.coef.ch[inf.cset], c2 = a.coef.c2[inf.cset];
     const float ebar = a.ebar, alpha = a.alpha;
     const bool want_kbp = a.kbp != nullptr;
 #pragma unroll 2
@@ -244,24 +310,6 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
         h0.y += (v.x - ebar) * bb.y;
         h1.x += (v.y - ebar) * bb.z;
         h1.y += (v.y - ebar) * bb.w;
-        if (kc != nullptr) {
-            const int g = z * N * N + o;
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int e0 = __ldg(a.pt_ptr + g + u), e1 = __ldg(a.pt_ptr + g + u + 1);
-                float2 acc = make_float2(0.f, 0.f);
-                for (int e = e0; e < e1; ++e) {
-                    const int at = __ldg(a.pt_atom + e);
-                    const float4 be = __ldg(a.pt_beta + e);
-                    const float4 c01 = ld4(kc + at * 4);
-                    const float4 c23 = ld4(kc + at * 4 + 2);
-                    acc.x += be.x * c01.x + be.y * c01.z + be.z * c23.x + be.w * c23.z;
-                    acc.y += be.x * c01.y + be.y * c01.w + be.z * c23.y + be.w * c23.w;
-                }
-                if (u == 0) h0 = cadd(h0, acc);
-                else h1 = cadd(h1, acc);
-            }
-        }
         if (dV != nullptr) {
             const float2 d = __ldg(reinterpret_cast<const float2*>(dV + o));
             const float4 pb = ld4(bp + o);
@@ -290,16 +338,15 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
     if (want_kbp) {
         // partial projections of `out` on this plane: one warp per (plane, atom) slot sums the
         // atom's support points in the plane from shared memory, in a fixed order
-        const int s0 = __ldg(a.plane_off + z), s1 = __ldg(a.plane_off + z + 1);
+        const int sb = __ldg(a.plane_off + z), s1 = __ldg(a.plane_off + z + 1);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int zo = z * N * N;
-        for (int k = s0 + warp; k < s1; k += NT / 32) {
+        for (int k = sb + warp; k < s1; k += NT / 32) {
             float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const int e1 = __ldg(a.slot_end + k);
-            for (int e = __ldg(a.slot_beg + k) + lane; e < e1; e += 32) {
-                const int o = __ldg(a.sup_idx + e) - zo;
+            const int e1 = __ldg(a.kbe_slot_end + k);
+            for (int e = __ldg(a.kbe_slot_beg + k) + lane; e < e1; e += 32) {
+                const int o = (int)(__ldg(a.kbe_os + e) & 0xffffu);
                 const float2 v = sm[(o / N) * P + (o % N)];
-                const float4 be = __ldg(a.sup_beta + e);
+                const float4 be = __ldg(a.kbe_beta + e);
                 acc[0] += be.x * v.x; acc[1] += be.x * v.y;
                 acc[2] += be.y * v.x; acc[3] += be.y * v.y;
                 acc[4] += be.z * v.x; acc[5] += be.z * v.y;
@@ -453,13 +500,21 @@ template <int N> static cudaError_t set_attrs() {
     const int ps = (int)Cfg<N>::PLANE_SMEM;
     const int mx = (int)cudaSharedmemCarveoutMaxShared;
     if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
-    if ((e = cudaFuncSetAttribute(k_plane_step<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  mx)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                  mx)))
+        return e;
     if ((e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_density_fwd<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_pencil<N, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_pencil<N, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
-    if ((e = cudaFuncSetAttribute(k_plane_step<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)))
+        return e;
     if ((e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     if ((e = cudaFuncSetAttribute(k_density_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     return e;
@@ -484,17 +539,55 @@ cudaError_t grid_init_attributes(int n) {
         default: break;                                 \
     }
 
+// Resident CTAs per SM of the two passes of a Chebyshev term (for the launch-order lookahead)
+// Dynamic shared memory of the fused plane step: the plane plus 4 projections per KB slot
+size_t plane_step_smem(int n, int max_plane_slots) {
+    return sizeof(float2) * ((size_t)n * (n + 1) + 4 * (size_t)max_plane_slots);
+}
+
+cudaError_t plane_step_reserve_smem(int n, size_t bytes) {
+    cudaError_t e = cudaSuccess;
+    SGW_DISPATCH_N(n, {
+        e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)bytes);
+    });
+    return e;
+}
+
+int plane_step_blocks_per_sm(int n, int variant, int max_plane_slots) {
+    int r = 0;
+    const size_t sm = plane_step_smem(n, max_plane_slots);
+    SGW_DISPATCH_N(n, {
+        if (variant == 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_plane_step<N, Cfg<N>::PLANE_NT>, Cfg<N>::PLANE_NT, sm);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_plane_step<N, Cfg<N>::PLANE_NT2>, Cfg<N>::PLANE_NT2, sm);
+    });
+    return r;
+}
+
+int pencil_blocks_per_sm(int n) {
+    int r = 0;
+    SGW_DISPATCH_N(n, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_pencil<N, 0>, Cfg<N>::PENCIL_NT,
+                                                                    Cfg<N>::PENCIL_SMEM));
+    return r;
+}
+
 void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st) {
     SGW_DISPATCH_N(n, k_plane_fwd<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(in, W, tw));
 }
 
-void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st) {
+void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st,
+                   int pf_ahead) {
     SGW_DISPATCH_N(n, {
         const dim3 grid((N / Cfg<N>::TX) * N, batch);
         if (kind == 0)
-            k_pencil<N, 0><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw);
+            k_pencil<N, 0><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw, pf_ahead);
         else
-            k_pencil<N, 1><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw);
+            k_pencil<N, 1><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw, pf_ahead);
     });
 }
 
@@ -506,8 +599,14 @@ void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, fl
     });
 }
 
-void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st) {
-    SGW_DISPATCH_N(n, k_plane_step<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(a, tw));
+void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
+    const size_t sm = plane_step_smem(n, a.kbc != nullptr ? a.max_plane_slots : 0);
+    SGW_DISPATCH_N(n, {
+        if (variant == 0)
+            k_plane_step<N, Cfg<N>::PLANE_NT><<<dim3(N, batch), Cfg<N>::PLANE_NT, sm, st>>>(a, tw);
+        else
+            k_plane_step<N, Cfg<N>::PLANE_NT2><<<dim3(N, batch), Cfg<N>::PLANE_NT2, sm, st>>>(a, tw);
+    });
 }
 
 void launch_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c,

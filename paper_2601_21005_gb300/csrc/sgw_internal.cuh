@@ -30,20 +30,24 @@ struct KBDev {
     int* sup_idx = nullptr;      // [n_sup]
     float4* sup_beta = nullptr;  // [n_sup]   beta_a0..3 at each support point
     float4* atom_e = nullptr;    // [n_atoms] E_a0..3
-    // point-major view for the apply
-    int* pt_ptr = nullptr;       // [ng + 1]
-    int* pt_atom = nullptr;      // [n_sup]
-    float4* pt_beta = nullptr;   // [n_sup]
     // per-plane partial projections: plane z owns slots plane_off[z] .. plane_off[z+1]-1, one per
-    // atom whose support meets the plane; slot k covers the atom-major support entries
-    // slot_beg[k] .. slot_end[k]-1 (the atom's points in that plane, contiguous because each
-    // atom's support is sorted by grid index); atom a's slots (in increasing z) are
-    // atom_pos[atom_pos_off[a] .. atom_pos_off[a+1]).
+    // atom whose support meets the plane (slot_atom[k] is that atom); atom a's slots (in
+    // increasing z) are atom_pos[atom_pos_off[a] .. atom_pos_off[a+1]).
     int total_slots = 0;
     int max_plane_slots = 0;
-    int* slot_beg = nullptr;     // [total_slots]
-    int* slot_end = nullptr;     // [total_slots]
     int* plane_off = nullptr;    // [n + 1]
+    int* slot_atom = nullptr;    // [total_slots]
+    // plane-major entries of the fused apply and projections.  The slots of a plane are split into
+    // colours whose point sets in the plane are disjoint; plane z's colour c holds the entries
+    // kbe_col[z (max_colors+1) + c] .. kbe_col[z (max_colors+1) + c + 1] - 1, slot by slot
+    // (slot k: kbe_slot_beg[k] .. kbe_slot_end[k] - 1).  Entry e: kbe_os[e] = in-plane offset |
+    // (plane-local slot << 16), kbe_beta[e] = the slot atom's beta_0..3 at that point.
+    int max_colors = 0;
+    int* kbe_col = nullptr;      // [n][max_colors + 1]
+    unsigned* kbe_os = nullptr;  // [n_sup]
+    float4* kbe_beta = nullptr;  // [n_sup]
+    int* kbe_slot_beg = nullptr; // [total_slots]
+    int* kbe_slot_end = nullptr; // [total_slots]
     int* atom_pos_off = nullptr; // [n_atoms + 1]
     int* atom_pos = nullptr;     // [total_slots]
 };
@@ -59,33 +63,44 @@ struct StepArgs {
     const float* dvpot;     // [rows][ng] or nullptr
     const VecInfo* info;    // [B]
     const float2* kbc;      // [B][n_proj] E-weighted projector coefficients (nullptr: no KB)
-    const int* pt_ptr;
-    const int* pt_atom;
-    const float4* pt_beta;
+    // KB tables (see KBDev)
+    const int* plane_off;
+    const int* slot_atom;
+    const int* kbe_col;
+    const unsigned* kbe_os;
+    const float4* kbe_beta;
+    const int* kbe_slot_beg;
+    const int* kbe_slot_end;
+    int max_colors;
+    int max_plane_slots;
     // partial projections of `out` (nullptr: skip): kbp[b][slot][4] = sum_plane beta_ap(r) out(r)
     float2* kbp;
-    const int* sup_idx;
-    const float4* sup_beta;
-    const int* slot_beg;
-    const int* slot_end;
-    const int* plane_off;
     int total_slots;
     int n_proj;
     float ebar, alpha;
     StepCoef coef;
+    // L2 prefetch of the W plane of the block this many blocks later in launch order (0: off);
+    // a performance hint only, results do not depend on it
+    int pf_ahead;
+    // 1: prefetch this block's pointwise operands into L2 at its start (a hint as well)
+    int pf_operands;
 };
 
 // ---- grid kernels (kernels_grid.cu)
 bool grid_supported(int n);
 cudaError_t grid_init_attributes(int n);
+int plane_step_blocks_per_sm(int n, int variant, int max_plane_slots);
+size_t plane_step_smem(int n, int max_plane_slots);
+cudaError_t plane_step_reserve_smem(int n, size_t bytes);
+int pencil_blocks_per_sm(int n);
 void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st);
 // kind: 0 kinetic (T(k)/N^3, capped at ecut if ecut > 0), 1 Coulomb (4 pi/k^2 / N^3, k=0 -> 0)
 void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw,
-                   cudaStream_t st);
+                   cudaStream_t st, int pf_ahead = 0);
 // exchange energy: acc[b / per] += (dV / N) sum_k v(k) |F(k)|^2 after the z transform
 void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
                                   const float2* tw, double* acc, cudaStream_t st);
-void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st);
+void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant = 0);
 // inverse xy transform of W, epilogue: mode 0 -> out_c[b] = plane (c64);
 // mode 1 (Poisson of TDH densities) -> vtot[b] = vloc + Re, dv[b] = Im, uR[b] = Im (if uR)
 void launch_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c,

@@ -22,6 +22,9 @@ def main():
     ap.add_argument('--steps', type=int, default=2)
     ap.add_argument('--deg', type=int, default=16)
     ap.add_argument('--no-kb', action='store_true')
+    ap.add_argument('--tune', default=None,
+                    help='semicolon-separated settings "operands,plane_lookahead,pencil_lookahead" to time in turn')
+    ap.add_argument('--autotune', action='store_true', help='run the library autotuner first and report its choice')
     args = ap.parse_args()
     build.build()
     s = synth.si_cluster(n=args.n, h=0.5, radius=10.5 if args.n >= 64 else 4.5)
@@ -32,18 +35,28 @@ def main():
     ng = args.n ** 3
     psi = torch.empty(args.batch, ng, dtype=torch.complex64, device='cuda')
     ctx.white_noise(5, 3, 0, 1, args.batch, psi)
-    ctx.propagate(psi, 1, 0.05, args.deg)          # warm-up
-    torch.cuda.synchronize()
-    ctx.profile(True)
-    ctx.propagate(psi, args.steps, 0.05, args.deg)
-    prof = ctx.profile_read()
-    ctx.profile(False)
-    out = {}
-    for k, v in prof.items():
-        if v['launches']:
-            out[k] = dict(launches=v['launches'], avg_us=round(1e3 * v['ms'] / v['launches'], 2),
-                          alg_GBps=round(v['alg_bytes'] / (v['ms'] * 1e-3) / 1e9, 1) if v['alg_bytes'] else None)
-    print(json.dumps(dict(n=args.n, batch=args.batch, steps=args.steps, deg=args.deg, kernels=out)))
+    chosen = ctx.autotune(args.batch) if args.autotune else None
+    settings = [None]
+    if args.tune:
+        settings = [tuple(int(v) for v in t.split(',')) for t in args.tune.split(';')]
+    for st in settings:
+        if st is not None:
+            for k, v in enumerate(st):
+                ctx.set_tuning(k, v)
+        tuning = [ctx.get_tuning(k) for k in range(ctx.TUNE_KEYS)]
+        ctx.propagate(psi, 1, 0.05, args.deg)          # warm-up
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        ctx.propagate(psi, args.steps, 0.05, args.deg)
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        out = {}
+        for k, v in prof.items():
+            if v['launches']:
+                out[k] = dict(launches=v['launches'], avg_us=round(1e3 * v['ms'] / v['launches'], 2),
+                              alg_GBps=round(v['alg_bytes'] / (v['ms'] * 1e-3) / 1e9, 1) if v['alg_bytes'] else None)
+        print(json.dumps(dict(n=args.n, batch=args.batch, steps=args.steps, deg=args.deg, tuning=tuning,
+                              autotuned=chosen, kernels=out)), flush=True)
 
 
 if __name__ == '__main__':

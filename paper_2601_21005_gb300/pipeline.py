@@ -18,7 +18,8 @@ from . import sgw as _sgw
 class Pipeline:
     def __init__(self, n, h, vloc, kb_atoms, phi, e_homo, e_lumo, n_eta=8, n_steps=200, dt=0.05,
                  cheb_deg=16, n_cheb=128, samples_per_batch=1, seed=1000, stream_id=1, device=0, ecut=0.0,
-                 spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None, graphs=False):
+                 spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None, graphs=False,
+                 autotune=False):
         import torch
         self.torch = torch
         # CUDA graphs need a non-default stream: the pipeline then owns one, and its buffers are
@@ -44,6 +45,8 @@ class Pipeline:
             self.emin, self.emax = spectrum
             self.ctx.set_spectrum(self.emin, self.emax)
         self.e_homo, self.e_lumo = e_homo, e_lumo
+        # launch hints timed on this GPU with the TDH batch size (results do not depend on them)
+        self.tuning = self.ctx.autotune(min(mb, 2 * self.ns * n_eta)) if autotune else None
         if coeffs is None:
             coeffs = _sgw.sgw_gapped_filter_coeffs(e_homo, e_lumo, self.emin, self.emax, n_cheb)
         self.coeffs = np.asarray(coeffs, dtype=np.float64)

@@ -35,6 +35,9 @@ _SIGS = {
     'sgw_destroy': ([_P], None),
     'sgw_set_stream': ([_P, _P], _c.c_int),
     'sgw_set_graph_mode': ([_P, _c.c_int], _c.c_int),
+    'sgw_set_tuning': ([_P, _c.c_int, _c.c_int], _c.c_int),
+    'sgw_get_tuning': ([_P, _c.c_int, _P], _c.c_int),
+    'sgw_autotune': ([_P, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_set_potential': ([_P, _P, _c.c_int, _P, _P, _P, _P, _P], _c.c_int),
     'sgw_apply_h': ([_P, _P, _P, _c.c_int], _c.c_int),
     'sgw_spectral_bounds': ([_P, _c.c_int, _c.c_uint64, _c.c_double, _P, _P, _P], _c.c_int),
@@ -270,6 +273,22 @@ class Context:
 
     def set_graph_mode(self, enable):
         self._ck('sgw_set_graph_mode', lib().sgw_set_graph_mode(self._p, 1 if enable else 0))
+
+    TUNE_PLANE_OPERANDS, TUNE_PLANE_LOOKAHEAD, TUNE_PENCIL_LOOKAHEAD, TUNE_PLANE_THREADS, TUNE_KEYS = 0, 1, 2, 3, 4
+
+    def set_tuning(self, key, value):
+        self._ck('sgw_set_tuning', lib().sgw_set_tuning(self._p, int(key), int(value)))
+
+    def get_tuning(self, key):
+        v = _c.c_int(0)
+        self._ck('sgw_get_tuning', lib().sgw_get_tuning(self._p, int(key), _c.byref(v)))
+        return v.value
+
+    def autotune(self, batch, reps=3):
+        """Time the candidate lookaheads on a scratch batch; returns the chosen value per key."""
+        out = (_c.c_int * self.TUNE_KEYS)()
+        self._ck('sgw_autotune', lib().sgw_autotune(self._p, int(batch), int(reps), out))
+        return list(out)
 
     def set_potential(self, vloc_dev, kb_atoms=()):
         """kb_atoms: list of (support flat indices, beta [n_proj, n_sup], e [n_proj])."""
