@@ -75,6 +75,70 @@ __device__ __forceinline__ void fft2_plane(float2* sm, const float2* __restrict_
     fft_lines<N, N, P, 1, NT, DIR>(sm, tw);   // along x: line = y, element stride = 1
 }
 
+// Radix of the last stage of an n-point transform (same plan as NextRadix)
+constexpr int last_radix(int n) {
+    int ns = 1, r = 1;
+    while (ns < n) {
+        const int rem = n / ns;
+        r = rem == 16 ? 4 : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2));
+        ns *= r;
+    }
+    return r;
+}
+
+// Stages with sub-length NS in [NS, NSTOP)
+template <int N, int NS, int NSTOP, int NL, int LS, int ES, int NT, int DIR>
+__device__ __forceinline__ void fft_rec_until(float2* s, const float2* __restrict__ tw) {
+    if constexpr (NS < NSTOP) {
+        constexpr int R = NextRadix<N / NS>::value;
+        fft_stage<N, R, NS, NL, LS, ES, NT, DIR>(s, tw);
+        fft_rec_until<N, NS * R, NSTOP, NL, LS, ES, NT, DIR>(s, tw);
+    }
+}
+
+// Inverse xy transform of a plane read from global memory: the first stage along y takes its
+// inputs straight from global (consecutive threads on consecutive x: coalesced rows), the
+// remaining stages run in shared memory; the result is left in sm (pitch N + 1).
+template <int N, int NT>
+__device__ __forceinline__ void inv_plane_from_global(float2* sm, const float2* __restrict__ src,
+                                                      const float2* __restrict__ tw) {
+    constexpr int P = N + 1, R1 = NextRadix<N>::value, NB = N / R1, TOT = N * NB, PER = (TOT + NT - 1) / NT;
+    float2 v[PER][R1];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * NT;
+        if (TOT % NT == 0 || b < TOT) {
+            const int l = b % N, j = b / N;
+#pragma unroll
+            for (int r = 0; r < R1; ++r) v[p][r] = __ldg(src + (j + r * NB) * N + l);
+        }
+    }
+    stage_r2s<N, R1, 1, N, 1, P, NT, +1>(v, sm, tw);
+    fft_rec<N, R1, N, 1, P, NT, +1>(sm, tw);            // the other stages along y
+    fft_lines<N, N, P, 1, NT, +1>(sm, tw);              // along x
+}
+
+// Forward xy transform of the plane in sm, written to global memory: along x, then along y
+// with the last stage's outputs stored straight from registers (coalesced rows).
+template <int N, int NT>
+__device__ __forceinline__ void fwd_plane_to_global(float2* sm, float2* __restrict__ dst,
+                                                    const float2* __restrict__ tw) {
+    constexpr int P = N + 1, RL = last_radix(N), NS = N / RL, TOT = N * NS, PER = (TOT + NT - 1) / NT;
+    fft_lines<N, N, P, 1, NT, -1>(sm, tw);              // along x
+    fft_rec_until<N, 1, NS, N, 1, P, NT, -1>(sm, tw);   // along y but the last stage
+    float2 c[PER][RL];
+    stage_s2r<N, RL, NS, N, 1, P, NT, -1>(sm, c, tw);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int b = threadIdx.x + p * NT;
+        if (TOT % NT == 0 || b < TOT) {
+            const int l = b % N, j = b / N;
+#pragma unroll
+            for (int q = 0; q < RL; ++q) dst[(j + q * NS) * N + l] = c[p][q];
+        }
+    }
+}
+
 // ------------------------------------------------------------------ forward plane pass
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
@@ -84,8 +148,7 @@ k_plane_fwd(const float2* __restrict__ in, float2* __restrict__ W, const float2*
     const size_t plane = ((size_t)blockIdx.y * N + blockIdx.x) * N * N;
     load_plane<N, NT>(sm, in + plane);
     __syncthreads();
-    fft2_plane<N, NT, -1>(sm, tw);
-    store_plane<N, NT>(W + plane, sm);
+    fwd_plane_to_global<N, NT>(sm, W + plane, tw);
 }
 
 // ------------------------------------------------------------------ pencil pass
@@ -272,9 +335,7 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
         const int ns = __ldg(a.plane_off + z + 1) - s0;
         for (int i = threadIdx.x; i < 4 * ns; i += NT) kcs[i] = kc[__ldg(a.slot_atom + s0 + i / 4) * 4 + (i & 3)];
     }
-    load_plane<N, NT>(sm, a.W + plane);
-    __syncthreads();
-    fft2_plane<N, NT, +1>(sm, tw);
+    inv_plane_from_global<N, NT>(sm, a.W + plane, tw);
     if (kc != nullptr) {
         // KB apply, colour by colour: within a colour every point occurs once, so the adds need no
         // atomics and their order at a point (colour order) is fixed
@@ -358,8 +419,7 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
             if (lane < 8) reinterpret_cast<float*>(a.kbp + ((size_t)b * a.total_slots + k) * 4)[lane] = acc[lane];
         }
     }
-    fft2_plane<N, NT, -1>(sm, tw);
-    store_plane<N, NT>(a.Wout + plane, sm);
+    fwd_plane_to_global<N, NT>(sm, a.Wout + plane, tw);
 }
 
 // ------------------------------------------------------------------ inverse plane pass
@@ -372,9 +432,7 @@ k_plane_inv(const float2* __restrict__ W, const float2* __restrict__ tw, int mod
     constexpr size_t NG = (size_t)N * N * N;
     const int z = blockIdx.x, b = blockIdx.y;
     const size_t plane = ((size_t)b * N + z) * N * N;
-    load_plane<N, NT>(sm, W + plane);
-    __syncthreads();
-    fft2_plane<N, NT, +1>(sm, tw);
+    inv_plane_from_global<N, NT>(sm, W + plane, tw);
     if (mode == 0) {
         store_plane<N, NT>(out_c + plane, sm);
         return;
@@ -426,8 +484,7 @@ k_density_fwd(const float2* __restrict__ psi, int n_eta, float weight, float* rh
         sm[y * P + x + 1] = make_float2(r1 - rz[1], d1);
     }
     __syncthreads();
-    fft2_plane<N, NT, -1>(sm, tw);
-    store_plane<N, NT>(Wp + ((size_t)s * N + z) * N * N, sm);
+    fwd_plane_to_global<N, NT>(sm, Wp + ((size_t)s * N + z) * N * N, tw);
 }
 
 // ------------------------------------------------------------------ KB projection
