@@ -71,6 +71,14 @@ template <int DIR> struct Dft<8, DIR> {
     }
 };
 
+// Twiddle table access: a plain pointer is a global table read through the read-only path;
+// TwShared wraps a copy of the table in shared memory.
+struct TwShared {
+    const float2* p;
+};
+__device__ __forceinline__ float2 tw_at(const float2* __restrict__ t, int i) { return __ldg(t + i); }
+__device__ __forceinline__ float2 tw_at(TwShared t, int i) { return t.p[i]; }
+
 // Radix of the next stage given the remaining length: 8 while possible, except that
 // 16 splits as 4 x 4 (fewer registers, same passes).
 template <int REM> struct NextRadix {
@@ -80,8 +88,8 @@ template <int REM> struct NextRadix {
 // One Stockham stage over NL lines.  Element e of line l is at s[l*LS + e*ES].
 // Consecutive threads take consecutive lines (conflict-free for the layouts used here).
 // tw: table exp(-2 pi i m / N), m < N (read through the read-only cache).
-template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR>
-__device__ __forceinline__ void fft_stage(float2* s, const float2* __restrict__ tw) {
+template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR, class TW>
+__device__ __forceinline__ void fft_stage(float2* s, TW tw) {
     constexpr int NB = N / R;
     constexpr int TOT = NL * NB;
     constexpr int PER = (TOT + NT - 1) / NT;
@@ -106,7 +114,7 @@ __device__ __forceinline__ void fft_stage(float2* s, const float2* __restrict__ 
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[(r * k * TWS) & (N - 1)]);
+                    float2 w = tw_at(tw, (r * k * TWS) & (N - 1));
                     if (DIR > 0) w.y = -w.y;
                     v[p][r] = cmul(v[p][r], w);
                 }
@@ -120,8 +128,8 @@ __device__ __forceinline__ void fft_stage(float2* s, const float2* __restrict__ 
     __syncthreads();
 }
 
-template <int N, int NS, int NL, int LS, int ES, int NT, int DIR>
-__device__ __forceinline__ void fft_rec(float2* s, const float2* __restrict__ tw) {
+template <int N, int NS, int NL, int LS, int ES, int NT, int DIR, class TW>
+__device__ __forceinline__ void fft_rec(float2* s, TW tw) {
     if constexpr (NS < N) {
         constexpr int R = NextRadix<N / NS>::value;
         fft_stage<N, R, NS, NL, LS, ES, NT, DIR>(s, tw);
@@ -131,8 +139,8 @@ __device__ __forceinline__ void fft_rec(float2* s, const float2* __restrict__ tw
 
 // NL independent N-point FFTs (N a power of two, 2..4096) in shared memory.
 // Caller must __syncthreads() before (data ready); returns after a barrier.
-template <int N, int NL, int LS, int ES, int NT, int DIR>
-__device__ __forceinline__ void fft_lines(float2* s, const float2* __restrict__ tw) {
+template <int N, int NL, int LS, int ES, int NT, int DIR, class TW>
+__device__ __forceinline__ void fft_lines(float2* s, TW tw) {
     fft_rec<N, 1, NL, LS, ES, NT, DIR>(s, tw);
 }
 
@@ -145,8 +153,8 @@ __device__ __forceinline__ void fft_lines(float2* s, const float2* __restrict__ 
 // Butterfly b = threadIdx.x + p NT of a stage maps to line l = b % NL, index j = b / NL.
 
 // Stage with inputs in registers v[p][r] (= x[l][j + r N/R] before twiddles), outputs to smem.
-template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR, int PER>
-__device__ __forceinline__ void stage_r2s(float2 (&v)[PER][R], float2* s, const float2* __restrict__ tw) {
+template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR, int PER, class TW>
+__device__ __forceinline__ void stage_r2s(float2 (&v)[PER][R], float2* s, TW tw) {
     constexpr int NB = N / R;
     constexpr int TOT = NL * NB;
     constexpr int TWS = N / (NS * R);
@@ -160,7 +168,7 @@ __device__ __forceinline__ void stage_r2s(float2 (&v)[PER][R], float2* s, const 
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[(r * k * TWS) & (N - 1)]);
+                    float2 w = tw_at(tw, (r * k * TWS) & (N - 1));
                     if (DIR > 0) w.y = -w.y;
                     v[p][r] = cmul(v[p][r], w);
                 }
@@ -176,8 +184,8 @@ __device__ __forceinline__ void stage_r2s(float2 (&v)[PER][R], float2* s, const 
 
 // Last stage (NS * R == N) with inputs from smem and outputs kept in registers:
 // v[p][q] = y[l][j + q NS].  Ends with a barrier so that smem may be overwritten.
-template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR, int PER>
-__device__ __forceinline__ void stage_s2r(const float2* s, float2 (&v)[PER][R], const float2* __restrict__ tw) {
+template <int N, int R, int NS, int NL, int LS, int ES, int NT, int DIR, int PER, class TW>
+__device__ __forceinline__ void stage_s2r(const float2* s, float2 (&v)[PER][R], TW tw) {
     constexpr int NB = N / R;
     constexpr int TOT = NL * NB;
     constexpr int TWS = N / (NS * R);
@@ -194,7 +202,7 @@ __device__ __forceinline__ void stage_s2r(const float2* s, float2 (&v)[PER][R], 
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = __ldg(&tw[(r * k * TWS) & (N - 1)]);
+                    float2 w = tw_at(tw, (r * k * TWS) & (N - 1));
                     if (DIR > 0) w.y = -w.y;
                     v[p][r] = cmul(v[p][r], w);
                 }

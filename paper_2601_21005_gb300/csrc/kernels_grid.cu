@@ -68,8 +68,8 @@ __device__ __forceinline__ void store_plane(float2* __restrict__ dst, const floa
     }
 }
 
-template <int N, int NT, int DIR>
-__device__ __forceinline__ void fft2_plane(float2* sm, const float2* __restrict__ tw) {
+template <int N, int NT, int DIR, class TW>
+__device__ __forceinline__ void fft2_plane(float2* sm, TW tw) {
     constexpr int P = N + 1;
     fft_lines<N, N, 1, P, NT, DIR>(sm, tw);   // along y: line = x, element stride = pitch
     fft_lines<N, N, P, 1, NT, DIR>(sm, tw);   // along x: line = y, element stride = 1
@@ -87,21 +87,20 @@ constexpr int last_radix(int n) {
 }
 
 // Stages with sub-length NS in [NS, NSTOP)
-template <int N, int NS, int NSTOP, int NL, int LS, int ES, int NT, int DIR>
-__device__ __forceinline__ void fft_rec_until(float2* s, const float2* __restrict__ tw) {
+template <int N, int NS, int NSTOP, int NL, int LS, int ES, int NT, int DIR, class TW>
+__device__ __forceinline__ void fft_rec_until(float2* s, TW tw) {
     if constexpr (NS < NSTOP) {
         constexpr int R = NextRadix<N / NS>::value;
         fft_stage<N, R, NS, NL, LS, ES, NT, DIR>(s, tw);
-        fft_rec_until<N, NS * R, NSTOP, NL, LS, ES, NT, DIR>(s, tw);
+        fft_rec_until<N, NS * R, NSTOP, NL, LS, ES, NT, DIR, TW>(s, tw);
     }
 }
 
 // Inverse xy transform of a plane read from global memory: the first stage along y takes its
 // inputs straight from global (consecutive threads on consecutive x: coalesced rows), the
 // remaining stages run in shared memory; the result is left in sm (pitch N + 1).
-template <int N, int NT>
-__device__ __forceinline__ void inv_plane_from_global(float2* sm, const float2* __restrict__ src,
-                                                      const float2* __restrict__ tw) {
+template <int N, int NT, class TW>
+__device__ __forceinline__ void inv_plane_from_global(float2* sm, const float2* __restrict__ src, TW tw) {
     constexpr int P = N + 1, R1 = NextRadix<N>::value, NB = N / R1, TOT = N * NB, PER = (TOT + NT - 1) / NT;
     float2 v[PER][R1];
 #pragma unroll
@@ -120,9 +119,8 @@ __device__ __forceinline__ void inv_plane_from_global(float2* sm, const float2* 
 
 // Forward xy transform of the plane in sm, written to global memory: along x, then along y
 // with the last stage's outputs stored straight from registers (coalesced rows).
-template <int N, int NT>
-__device__ __forceinline__ void fwd_plane_to_global(float2* sm, float2* __restrict__ dst,
-                                                    const float2* __restrict__ tw) {
+template <int N, int NT, class TW>
+__device__ __forceinline__ void fwd_plane_to_global(float2* sm, float2* __restrict__ dst, TW tw) {
     constexpr int P = N + 1, RL = last_radix(N), NS = N / RL, TOT = N * NS, PER = (TOT + NT - 1) / NT;
     fft_lines<N, N, P, 1, NT, -1>(sm, tw);              // along x
     fft_rec_until<N, 1, NS, N, 1, P, NT, -1>(sm, tw);   // along y but the last stage
@@ -327,15 +325,19 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
         const long nxt = (long)b * N + z + a.pf_ahead;         // linear id of a later block
         if (nxt < (long)gridDim.y * N) l2_prefetch(a.W + (size_t)nxt * N * N, N * N * sizeof(float2));
     }
-    // E-weighted projections of b_{k+1} for the atoms of this plane's slots: kcs[slot][4]
-    float2* kcs = sm + N * P;
+    // twiddles and the E-weighted projections of b_{k+1} for the atoms of this plane's slots
+    // (kcs[slot][4]) next to the plane in shared memory
+    float2* stw = sm + N * P;
+    float2* kcs = stw + N;
+    for (int i = threadIdx.x; i < N; i += NT) stw[i] = __ldg(tw + i);
+    const TwShared tws{stw};
     const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
     const int s0 = kc != nullptr ? __ldg(a.plane_off + z) : 0;
     if (kc != nullptr) {
         const int ns = __ldg(a.plane_off + z + 1) - s0;
         for (int i = threadIdx.x; i < 4 * ns; i += NT) kcs[i] = kc[__ldg(a.slot_atom + s0 + i / 4) * 4 + (i & 3)];
     }
-    inv_plane_from_global<N, NT>(sm, a.W + plane, tw);
+    inv_plane_from_global<N, NT>(sm, a.W + plane, tws);
     if (kc != nullptr) {
         // KB apply, colour by colour: within a colour every point occurs once, so the adds need no
         // atomics and their order at a point (colour order) is fixed
@@ -419,7 +421,7 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
             if (lane < 8) reinterpret_cast<float*>(a.kbp + ((size_t)b * a.total_slots + k) * 4)[lane] = acc[lane];
         }
     }
-    fwd_plane_to_global<N, NT>(sm, a.Wout + plane, tw);
+    fwd_plane_to_global<N, NT>(sm, a.Wout + plane, tws);
 }
 
 // ------------------------------------------------------------------ inverse plane pass
@@ -523,34 +525,52 @@ k_kb_project(const int64_t* __restrict__ atom_off, const int* __restrict__ sup_i
     }
 }
 
-// kbc[b][4a + p] = E_ap dV sum_{slots of a} kbp[b][slot][p]  (fixed order: increasing plane)
-__global__ void k_kb_reduce(const int* __restrict__ atom_pos_off, const int* __restrict__ atom_pos,
-                            const float4* __restrict__ atom_e, const float2* __restrict__ kbp, int n_atoms, int batch,
-                            int total_slots, int n_proj, float dV, float2* __restrict__ kbc) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= batch * n_atoms * 4) return;
-    const int p = t & 3, a = (t >> 2) % n_atoms, b = (t >> 2) / n_atoms;
+// kbc[b][4a + p] = E_ap dV sum_{slots of a} kbp[b][slot][p].  One warp per (b, a): lane l takes
+// projector p = l % 4 of the atom's slots l / 4, l / 4 + 8, ... (in increasing plane), then the
+// eight lanes of each p are summed by a fixed shuffle tree.
+__global__ void __launch_bounds__(256)
+k_kb_reduce(const int* __restrict__ atom_pos_off, const int* __restrict__ atom_pos, const float4* __restrict__ atom_e,
+            const float2* __restrict__ kbp, int n_atoms, int batch, int total_slots, int n_proj, float dV,
+            float2* __restrict__ kbc) {
+    const int w = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (w >= batch * n_atoms) return;                     // whole warps leave together
+    const int a = w % n_atoms, b = w / n_atoms, p = lane & 3;
+    const int q0 = __ldg(atom_pos_off + a), q1 = __ldg(atom_pos_off + a + 1);
+    const float2* kb = kbp + (size_t)b * total_slots * 4;
     float2 acc = make_float2(0.f, 0.f);
-    const int q1 = __ldg(atom_pos_off + a + 1);
-    for (int q = __ldg(atom_pos_off + a); q < q1; ++q) {
-        const float2 v = __ldg(kbp + ((size_t)b * total_slots + __ldg(atom_pos + q)) * 4 + p);
+    for (int q = q0 + (lane >> 2); q < q1; q += 8) {
+        const float2 v = __ldg(kb + (size_t)__ldg(atom_pos + q) * 4 + p);
         acc.x += v.x;
         acc.y += v.y;
     }
-    const float4 e = __ldg(atom_e + a);
-    const float ep = (p == 0 ? e.x : (p == 1 ? e.y : (p == 2 ? e.z : e.w))) * dV;
-    kbc[(size_t)b * n_proj + a * 4 + p] = make_float2(ep * acc.x, ep * acc.y);
+#pragma unroll
+    for (int off = 4; off < 32; off <<= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane < 4) {
+        const float4 e = __ldg(atom_e + a);
+        const float ep = (p == 0 ? e.x : (p == 1 ? e.y : (p == 2 ? e.z : e.w))) * dV;
+        kbc[(size_t)b * n_proj + a * 4 + p] = make_float2(ep * acc.x, ep * acc.y);
+    }
 }
 
 void launch_kb_reduce(const KBDev& kb, const float2* kbp, int batch, float dV, float2* kbc, cudaStream_t st) {
-    const int total = batch * kb.n_atoms * 4;
-    if (total == 0) return;
-    k_kb_reduce<<<(total + 255) / 256, 256, 0, st>>>(kb.atom_pos_off, kb.atom_pos, kb.atom_e, kbp, kb.n_atoms, batch,
-                                                    kb.total_slots, kb.n_proj, dV, kbc);
+    const long warps = (long)batch * kb.n_atoms;
+    if (warps == 0) return;
+    k_kb_reduce<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(kb.atom_pos_off, kb.atom_pos, kb.atom_e, kbp,
+                                                                     kb.n_atoms, batch, kb.total_slots, kb.n_proj, dV,
+                                                                     kbc);
 }
 
 // ------------------------------------------------------------------ launchers
 bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+
+// Dynamic shared memory of the fused plane step: the plane, the twiddle table and 4
+// projections per KB slot
+size_t plane_step_smem(int n, int max_plane_slots) {
+    return sizeof(float2) * ((size_t)n * (n + 2) + 4 * (size_t)max_plane_slots);
+}
 
 template <int N> static cudaError_t set_attrs() {
     cudaError_t e = cudaSuccess;
@@ -568,9 +588,10 @@ template <int N> static cudaError_t set_attrs() {
     if ((e = cudaFuncSetAttribute(k_pencil<N, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_pencil<N, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
-    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)))
+    const int pss = (int)plane_step_smem(N, 0);
+    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, pss)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps)))
+    if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pss)))
         return e;
     if ((e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     if ((e = cudaFuncSetAttribute(k_density_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
@@ -597,11 +618,6 @@ cudaError_t grid_init_attributes(int n) {
     }
 
 // Resident CTAs per SM of the two passes of a Chebyshev term (for the launch-order lookahead)
-// Dynamic shared memory of the fused plane step: the plane plus 4 projections per KB slot
-size_t plane_step_smem(int n, int max_plane_slots) {
-    return sizeof(float2) * ((size_t)n * (n + 1) + 4 * (size_t)max_plane_slots);
-}
-
 cudaError_t plane_step_reserve_smem(int n, size_t bytes) {
     cudaError_t e = cudaSuccess;
     SGW_DISPATCH_N(n, {
