@@ -15,6 +15,8 @@ zeta-bar_i, Eq. 4-5, so cheap functions of zeta-bar predict part of it):
   Coulomb-weighted quadratic forms behind Sigma_i and the exchange X_i);
 * network: layers h_1 = tanh(x W1 + b1), h_2 = tanh(h_1 W2 + b2), h_3 = tanh(h_2 W3 + b3),
   y = h_3 W4 + b4; loss = mean over samples and outputs of (y - t)^2; Adam;
+* linear part: an FP64 ridge regression of the targets on the per-shell sums of the features
+  (the network then fits what the linear part leaves); its normal equations are solved directly;
 * estimator: with M cheap samples (features only) and n paired samples (features and the
   plain Sigma_i), the rows z_i = mean_j f(x_j) + Y_i - f(x_i) have mean
   mean_j f(x_j) + mean_i (Y_i - f(x_i)), which is unbiased for E[Y] whatever f is, and
@@ -144,3 +146,47 @@ def standardize(a, mu=None, sd=None):
 def cv_rows(f_cheap, f_paired, y_paired):
     """Rows z_i = mean_j f(x_j) + Y_i - f(x_i) (their mean is the control-variate estimate)."""
     return np.mean(f_cheap, axis=0)[None, :] + y_paired - f_paired
+
+
+# ---------------------------------------------------------------- shell sums and the linear part
+def shells(m2max):
+    """Distinct |m|^2 values of the k list, increasing (the shells of the feature wave vectors)."""
+    return sorted(set(int(v) for v in (kset(m2max) ** 2).sum(axis=1)))
+
+
+def shell_count(m2max):
+    return 2 * (len(shells(m2max)) + 1)
+
+
+def shell_sums(feat, m2max):
+    """Per-shell sums of the per-k features: [zeta shells..., zeta k=0, eta shells..., eta k=0]."""
+    feat = np.atleast_2d(np.asarray(feat, dtype=np.float64))
+    ks = kset(m2max)
+    nk = len(ks)
+    sh = (ks ** 2).sum(axis=1)
+    out = []
+    for base in (0, nk + 1):
+        for s in shells(m2max):
+            out.append(feat[:, base:base + nk][:, sh == s].sum(axis=1))
+        out.append(feat[:, base + nk])
+    return np.stack(out, axis=1)
+
+
+def linear_fit(x, y, ridge):
+    """Ridge regression of y on standardised x: returns (mu_x, sd_x, ybar, B) with
+    (Xs^T Xs + ridge n I) B = Xs^T (y - ybar), Xs = (x - mu_x) / sd_x (sample sd; 1 where it is 0)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    n, p = x.shape
+    mu = x.mean(axis=0)
+    sd = x.std(axis=0, ddof=1) if n > 1 else np.zeros(p)
+    sd = np.where(sd > 0, sd, 1.0)
+    xs = (x - mu) / sd
+    ybar = y.mean(axis=0)
+    B = np.linalg.solve(xs.T @ xs + ridge * n * np.eye(p), xs.T @ (y - ybar))
+    return mu, sd, ybar, B
+
+
+def linear_apply(model, x):
+    mu, sd, ybar, B = model
+    return ybar + ((np.asarray(x, dtype=np.float64) - mu) / sd) @ B

@@ -114,3 +114,43 @@ def test_cv_estimator_unbiased_and_variance_reduced():
     # E[Y] = 3; the spread of the estimates matches the SE of Y - f plus Var(f)/M
     assert abs(est.mean() - 3.0) < 4 * est.std() / np.sqrt(len(est))
     assert np.mean(ses) < 0.5 * np.mean(plain_se)
+
+
+def test_shell_sums_by_hand():
+    # m2max = 3: shells 1 (3 vectors), 2 (6), 3 (4) -> 13 wave vectors, 8 shell features
+    assert mlp.shells(3) == [1, 2, 3]
+    assert mlp.shell_count(3) == 8
+    nk = len(mlp.kset(3))
+    assert nk == 13
+    f = np.arange(2 * (nk + 1), dtype=np.float64)[None, :] + 1.0
+    s = mlp.shell_sums(f, 3)[0]
+    # zeta block: entries 1..13 in shell order 3 x |m|^2=1, 6 x 2, 4 x 3, then k=0 entry 14
+    assert s[0] == 1 + 2 + 3 and s[1] == sum(range(4, 10)) and s[2] == sum(range(10, 14)) and s[3] == 14
+    assert s[4] == 15 + 16 + 17 and s[7] == 28
+    assert np.isclose(s.sum(), f.sum())                # every feature lands in exactly one sum
+
+
+def test_linear_fit_recovers_an_exact_linear_map():
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(40, 3)) * np.array([1.0, 10.0, 0.1]) + np.array([2.0, -1.0, 5.0])
+    A = rng.normal(size=(3, 4))
+    a0 = rng.normal(size=4)
+    y = a0 + x @ A
+    model = mlp.linear_fit(x, y, 0.0)
+    xt = rng.normal(size=(7, 3))
+    assert np.allclose(mlp.linear_apply(model, xt), a0 + xt @ A, atol=1e-10)
+
+
+def test_linear_fit_normal_equations_and_shrinkage():
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(30, 4))
+    y = rng.normal(size=(30, 2))
+    lam = 0.3
+    mu, sd, ybar, B = mlp.linear_fit(x, y, lam)
+    xs = (x - mu) / sd
+    # stationarity of sum |y - ybar - xs B|^2 + lam n |B|^2, written out independently
+    grad = -2 * xs.T @ (y - ybar - xs @ B) + 2 * lam * len(x) * B
+    assert np.max(np.abs(grad)) < 1e-10
+    assert np.allclose(xs.mean(0), 0, atol=1e-12) and np.allclose(xs.std(0, ddof=1), 1)
+    # stronger ridge shrinks the coefficients
+    assert np.linalg.norm(mlp.linear_fit(x, y, 10 * lam)[3]) < np.linalg.norm(B)
