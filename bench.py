@@ -32,11 +32,12 @@ HA_EV = 27.211386245988
 
 CONFIGS = {
     # the 64^3 cluster the metric is quoted on
-    'si35h36_64': dict(system='si_cluster', n=64, h=0.5, radius=10.5, samples_per_batch=4, n_eta=8,
+    'si35h36_64': dict(system='si_cluster', n=64, h=0.5, radius=10.5, samples_per_batch=4, zeta_group=4, n_eta=8,
                        n_steps=400, dt=0.05, cheb_deg=16, n_cheb=2000, workload='Si35H36 cluster, 64^3 grid '
-                       'h=0.5 bohr, 176 electrons, 64 orbitals (4 MC samples x 8 eta pairs) x 400 steps'),
+                       'h=0.5 bohr, 176 electrons, 64 orbitals per TDH launch (4 MC samples x 8 eta pairs) x '
+                       '400 steps; 16 MC samples per step, their 32 zeta vectors propagated together'),
     # the tiny periodic case (parity-test size)
-    'wells16': dict(system='wells', n=16, h=0.6, samples_per_batch=1, n_eta=8, n_steps=200, dt=0.05,
+    'wells16': dict(system='wells', n=16, h=0.6, samples_per_batch=1, zeta_group=1, n_eta=8, n_steps=200, dt=0.05,
                     cheb_deg=16, n_cheb=128, workload='6 Gaussian wells, 16^3 grid h=0.6 bohr, 8 electrons, '
                     '16 orbitals x 200 steps'),
 }
@@ -126,17 +127,29 @@ def kohn_sham_inputs(cfg, sysd, device):
                 raw_bounds=raw, eig_residual=res)
 
 
-def make_pipeline(cfg, sysd, ks, device, seed, fp64=True, graphs=False, autotune=False):
+def make_pipeline(cfg, sysd, ks, device, seed, fp64=True, graphs=False, autotune=False, zeta_group=None):
     from paper_2601_21005_gb300.pipeline import Pipeline
     return Pipeline(cfg['n'], cfg['h'], sysd['vloc'], sysd['kb_atoms'], ks['phi'], ks['e_homo'], ks['e_lumo'],
                     n_eta=cfg['n_eta'], n_steps=cfg['n_steps'], dt=cfg['dt'], cheb_deg=cfg['cheb_deg'],
                     n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'], seed=seed, stream_id=1,
-                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64, graphs=graphs, autotune=autotune)
+                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64, graphs=graphs, autotune=autotune,
+                    zeta_group=cfg['zeta_group'] if zeta_group is None else zeta_group)
+
+
+def step_samples(cfg):
+    """MC samples of one bench step (one pipeline run)."""
+    return cfg['samples_per_batch'] * cfg['zeta_group']
 
 
 def units_per_step(cfg):
-    """grid points x TDH-propagated orbitals x time steps of one batch."""
-    return cfg['n'] ** 3 * 2 * cfg['n_eta'] * cfg['samples_per_batch'] * cfg['n_steps']
+    """grid points x TDH-propagated orbitals x time steps of one bench step."""
+    return cfg['n'] ** 3 * 2 * cfg['n_eta'] * step_samples(cfg) * cfg['n_steps']
+
+
+# DRAM bytes (read + write, ncu) over algorithmic bytes of one 64-vector k_plane_step launch of the
+# current kernel (profiles/plane_step_pencil_64x64.md); traffic per launch = this ratio x the
+# launch's algorithmic bytes.  Must be re-measured whenever the plane kernel changes.
+PLANE_STEP_DRAM_PER_ALG = 831.6 / 806.4
 
 
 def roofline(prof, peaks):
@@ -149,7 +162,11 @@ def roofline(prof, peaks):
     peak = peaks['hbm_gbs']
     shares = {k: round(x['ms'] / total, 4) for k, x in prof.items() if x['launches']}
     return dict(bound='hbm', achieved=round(gbs, 1), peak=peak, unit='GB/s', frac=round(gbs / peak, 4),
-                traffic=None, kernel=name, launches=v['launches'], avg_launch_us=round(1e3 * v['ms'] / v['launches'], 2),
+                traffic=(round(PLANE_STEP_DRAM_PER_ALG * v['alg_bytes'] / v['launches'])
+                         if name == 'plane_step' else None),
+                traffic_source='ncu dram__bytes_read.sum + dram__bytes_write.sum of a 64-vector launch, '
+                               'scaled by algorithmic bytes to the average launch' if name == 'plane_step' else None,
+                kernel=name, launches=v['launches'], avg_launch_us=round(1e3 * v['ms'] / v['launches'], 2),
                 alg_bytes_per_launch=round(v['alg_bytes'] / v['launches']), peak_source=peaks['source'] + ' hbm_gbs',
                 time_shares=shares,
                 other_kernels={k: round(x['alg_bytes'] / (x['ms'] * 1e-3) / 1e9, 1) for k, x in kinds.items()})
@@ -214,7 +231,7 @@ def oracle_sample(cfg, n_filter_terms=2, n_tdh_steps=1, n_zeta_steps=1, seed=100
     t['time_order'] = (time.perf_counter() - t0) * g.ng / sl
     per_sample = (cfg['n_cheb'] * t['filter_term'] + N * (t['tdh_step'] + t['zeta_step']) + t['exchange']
                   + t['time_order'])
-    batch_s = cfg['samples_per_batch'] * per_sample
+    batch_s = step_samples(cfg) * per_sample
     measured = n_filter_terms * t['filter_term'] + n_tdh_steps * t['tdh_step'] + n_zeta_steps * t['zeta_step'] \
         + t['exchange'] + t['time_order'] * sl / g.ng
     return dict(value=units_per_step(cfg) / batch_s, batch_seconds=batch_s, measured_seconds=measured, parts=t)
@@ -236,7 +253,7 @@ def run_reference(args, cfg):
     sample = ('per step: 1 MC sample of %s -- %d filter terms on %d vectors, 1 TDH step of %d pairs, '
               '1 zeta step, exchange, time ordering of a 4096-point slice; extrapolated to the batch of %d '
               'samples x (N_chb=%d, N_tau=%d)' % (cfg['workload'], 2, cfg['n_eta'] + 1, cfg['n_eta'],
-                                                  cfg['samples_per_batch'], cfg['n_cheb'], cfg['n_steps']))
+                                                  step_samples(cfg), cfg['n_cheb'], cfg['n_steps']))
     line = dict(impl='reference', metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1e3 * statistics.median(meas), higher_is_better=True,
                 scaling='weak', vs_baseline=None, dtype='f64', data='synthetic',
@@ -288,7 +305,7 @@ def run_ours(args, cfg):
             np.savez(args.ks_cache, **{k: np.asarray(v) for k, v in ks.items()})
     pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs, autotune=args.autotune)
     t_setup = time.perf_counter() - t_setup
-    ns = cfg['samples_per_batch']
+    ns = step_samples(cfg)
     nb_total = args.warmup + args.steps
     sig = torch.empty(nb_total * ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
     xs = torch.empty(nb_total * ns, dtype=torch.float64, device='cuda')
@@ -378,7 +395,9 @@ def run_ours(args, cfg):
                 ms_per_step=ms_per_step, higher_is_better=True, scaling='weak', vs_baseline=None, dtype='c64/f32 + f64',
                 data='synthetic',
                 config=dict(workload=cfg['workload'], n_cheb=cfg['n_cheb'], cheb_deg=cfg['cheb_deg'], dt=cfg['dt'],
-                            samples_per_step=ns * world, l2='inputs larger than L2 (about 5 GB live per batch)',
+                            samples_per_step=ns * world, tdh_orbitals_per_launch=2 * cfg['n_eta'] * cfg['samples_per_batch'],
+                            zeta_vectors_per_launch=2 * ns,
+                            l2='inputs larger than L2 (about 20 GB live per step)',
                             precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world,
                             cuda_graphs=bool(args.graphs),
                             launch_tuning=dict(zip(('plane_operand_prefetch', 'plane_lookahead', 'pencil_lookahead',
@@ -399,14 +418,17 @@ def run_ours(args, cfg):
 def precision_comparison(cfg, sysd, ks, device, seed, pl, base):
     """Run one batch in the plain FP32 form and the same batch in the mixed form; QP difference."""
     import torch
-    pl32 = make_pipeline(cfg, sysd, ks, device, seed, fp64=False)
+    # one chunk of samples in the plain form; the mixed pipeline runs its whole step on the same
+    # first samples (per-sample results do not depend on how samples are grouped)
+    pl32 = make_pipeline(cfg, sysd, ks, device, seed, fp64=False, zeta_group=1)
     ns = cfg['samples_per_batch']
     out = {}
     for name, p in (('mixed_fp64', pl), ('plain_fp32', pl32)):
-        sg = torch.empty(ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
-        x = torch.empty(ns, dtype=torch.float64, device='cuda')
+        m = p.run_samples
+        sg = torch.empty(m, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
+        x = torch.empty(m, dtype=torch.float64, device='cuda')
         p.run_batch(base + 900000, sg, x)
-        out[name] = p.qp(sg, x, ks['e_homo'])['eps_qp']
+        out[name] = p.qp(sg[:ns].contiguous(), x[:ns].contiguous(), ks['e_homo'])['eps_qp']
     pl32.ctx.close()
     return dict(qp_eV_mixed=round(out['mixed_fp64'] * HA_EV, 6), qp_eV_plain_fp32=round(out['plain_fp32'] * HA_EV, 6),
                 diff_eV=abs(out['plain_fp32'] - out['mixed_fp64']) * HA_EV, samples=ns)
@@ -418,7 +440,7 @@ def cv_study(args, cfg, pl, ks, base):
     same paired samples."""
     import torch
     from paper_2601_21005_gb300.control_variate import ControlVariate
-    ns = cfg['samples_per_batch']
+    ns = pl.run_samples
     cv = ControlVariate(pl, m2max=10, width=256, max_batch=256, seed=11)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -476,7 +498,7 @@ def main():
                     help='keep the default launch hints instead of timing the candidates at setup')
     ap.add_argument('--cv', type=int, default=128, help='control-variate training samples (0: skip the study)')
     ap.add_argument('--cv-cheap', type=int, default=4096, help='cheap (features-only) samples in the study')
-    ap.add_argument('--cv-paired-batches', type=int, default=8, help='batches of paired samples in the study')
+    ap.add_argument('--cv-paired-batches', type=int, default=2, help='runs of paired samples in the study')
     ap.add_argument('--scale', type=float, default=1.0,
                     help='scale N_tau and N_chb together (profiling captures of fewer launches)')
     args = ap.parse_args()

@@ -343,6 +343,45 @@ sgw_status sgw_cv_rows(sgw_ctx* ctx, const float* f_cheap_dev, int n_cheap, cons
                        const double* sd_dev, double* rows_dev);
 
 /*
+ * Linear part of the control variate (not in the paper).  The per-k features of sgw_cv_features
+ * are summed per shell |m|^2 (the distinct |m|^2 <= m2max, increasing): out_dev[i] =
+ * [zeta-bar shell sums..., zeta-bar k = 0 feature, eta-bar shell sums..., eta-bar k = 0 feature]
+ * (float, sgw_cv_shell_count(m2max) = 2 (shells + 1) per sample; sums accumulated in FP64 in the
+ * features' k order).  feat_dev [n_samples][sgw_cv_feature_count(m2max)] (float).
+ */
+int sgw_cv_shell_count(int m2max);
+sgw_status sgw_cv_shell_sums(sgw_ctx* ctx, const float* feat_dev, int n_samples, int m2max, float* out_dev);
+
+/*
+ * FP64 ridge regression of targets y_dev [n][o] (double) on inputs x_dev [n][p] (float):
+ * mu, sd = column means and sample standard deviations of x (1 where 0), Xs = (x - mu) / sd,
+ * ybar = column means of y, and B solves (Xs^T Xs + ridge n I) B = Xs^T (y - ybar) (Gram and cross
+ * products on the GPU in FP64, Cholesky on the host in FP64).  model_dev (double, caller-owned,
+ * sgw_cv_linear_size(p, o) = 2p + o + p o entries) receives [mu][sd][ybar][B (p x o, row-major)].
+ * Needs n >= 2, 1 <= p <= 256, o >= 1, ridge >= 0 (SGW_EINVAL otherwise); SGW_ENOCONV when the
+ * normal matrix is not positive definite (ridge = 0 with dependent columns).  Synchronises.
+ */
+int64_t sgw_cv_linear_size(int p, int o);
+sgw_status sgw_cv_linear_fit(sgw_ctx* ctx, const float* x_dev, const double* y_dev, int n, int p, int o, double ridge,
+                             double* model_dev);
+
+/* f_ij = ybar_j + sum_a ((x_ia - mu_a) / sd_a) B_aj  (FP64) for x_dev [n][p] (float); out_dev [n][o]
+ * receives f, or y_dev - f (the residual of targets y_dev [n][o]) when y_dev is not NULL. */
+sgw_status sgw_cv_linear_apply(sgw_ctx* ctx, const double* model_dev, const float* x_dev, int n, int p, int o,
+                               const double* y_dev, double* out_dev);
+
+/*
+ * Rows of the linear control variate (FP64): y_out_dev[i][j] = y_i[j] - f(x_i)[j] + mean_m f(xc_m)[j]
+ * for the paired samples' inputs x_paired_dev [n_paired][p] and targets y_dev [n_paired][o] and
+ * the cheap samples' inputs x_cheap_dev [n_cheap][p] (the mean of a linear f is f at the mean
+ * input).  The rows' mean is unbiased for E[y] whatever the model; they can be combined further
+ * with sgw_cv_rows (network part) or passed to sgw_qp_energy.  n_cheap, n_paired >= 1.
+ */
+sgw_status sgw_cv_linear_rows(sgw_ctx* ctx, const double* model_dev, const float* x_cheap_dev, int n_cheap,
+                              const float* x_paired_dev, int n_paired, int p, int o, const double* y_dev,
+                              double* y_out_dev);
+
+/*
  * The network: h1 = tanh(x W1 + b1), h2 = tanh(h1 W2 + b2), h3 = tanh(h2 W3 + b3),
  * y = h3 W4 + b4, with n_in inputs, three hidden layers of `width`, n_out outputs.  FP32 master
  * weights and Adam state; the matrix products run on the tensor cores with BF16 operands

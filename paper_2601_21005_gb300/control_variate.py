@@ -2,17 +2,20 @@
 
 A sample's Sigma_i(t) (Eq. 5) and its sROI exchange X_i (Eq. 6) are quadratic forms in the
 sample's random vectors (zeta-bar_i and the eta-bar_il), so cheap features of those vectors --
-the Coulomb-weighted low-k power of zeta-bar_i phi and of eta-bar_il phi -- predict part of them.
+the Coulomb-weighted low-k power of zeta-bar_i phi and of eta-bar_il phi, summed per |k| shell --
+predict part of them.  The predictor is f = (FP64 ridge-linear part) + (network on its residual).
 The steps:
 
   collect : run plain samples (Pipeline.run_batch); targets Y_i = [Sigma_i(t) (2 (2N + 1) reals),
-            X_i], features x_i of the same samples;
-  train   : standardise inputs and targets (FP64 statistics), fit the network (GPU forward,
-            backward, Adam), keep the epoch with the lowest loss on a held-out part;
+            X_i], shell-summed features x_i of the same samples;
+  train   : fit the linear part on the training samples (FP64 normal equations), then the
+            network on the standardised residuals Y - f_lin(x) (GPU forward, backward, Adam),
+            keeping the epoch with the lowest held-out loss -- and the network only if that
+            loss beats predicting zero residual;
   estimate: with n new paired samples (Y_i, x_i) and M cheap samples (features only: the same
             Philox vectors of sample indices never run through the plain path), form the rows
             z_i = mean_j f(x_j) + Y_i - f(x_i) (FP64) and solve the QP equation on them.  The
-            estimate is unbiased for any network; with no cheap samples it is the plain one.
+            estimate is unbiased for any f; with no cheap samples it is the plain one.
 """
 import numpy as np
 
@@ -20,15 +23,20 @@ from . import sgw as _sgw
 
 
 class ControlVariate:
-    def __init__(self, pipeline, m2max=10, width=256, seed=77, max_batch=256):
+    def __init__(self, pipeline, m2max=10, width=256, seed=77, max_batch=256, ridge=1e-3):
         import torch
         self.torch = torch
         self.pl = pipeline
         self.m2max = m2max
-        self.n_feat = _sgw.sgw_cv_feature_count(m2max)
+        self.n_kfeat = _sgw.sgw_cv_feature_count(m2max)      # per-k features of the library
+        self.n_feat = _sgw.sgw_cv_shell_count(m2max)         # their shell sums: the model inputs
         self.n_sig = 2 * (2 * pipeline.n_steps + 1)
         self.n_out = self.n_sig + 1
         self.max_batch = max_batch
+        self.ridge = ridge
+        self.lin = torch.zeros(_sgw.sgw_cv_linear_size(self.n_feat, self.n_out), dtype=torch.float64,
+                               device=pipeline.dev)
+        self.use_net = True
         self.mlp = _sgw.MLP(self.n_feat, width, self.n_out, max_batch, seed=seed, device=pipeline.dev.index or 0,
                             stream=pipeline.stream.cuda_stream if pipeline.stream is not None else None)
         # X is one output against 2 (2N + 1) for Sigma(t) but carries a comparable share of the
@@ -52,17 +60,17 @@ class ControlVariate:
     def _collect(self, n_samples, sample0):
         """Plain samples sample0.. : (Y [n][n_out] f64 = [Sigma(t) interleaved, X], F [n][n_feat] f32)."""
         t, pl = self.torch, self.pl
-        ns = pl.ns
+        ns = pl.run_samples
         nb = (n_samples + ns - 1) // ns
         S = t.empty(nb * ns, 2 * pl.n_steps + 1, dtype=t.complex128, device=pl.dev)
         X = t.empty(nb * ns, dtype=t.float64, device=pl.dev)
-        F = t.empty(nb * ns, self.n_feat, dtype=t.float32, device=pl.dev)
         for b in range(nb):
             s0 = b * ns
             pl._run_batch(sample0 + s0, S[s0:s0 + ns], X[s0:s0 + ns])
-            pl.ctx.cv_features(pl.noise, ns, pl.n_eta + 1, pl.phi, self.m2max, F[s0:s0 + ns])
+        # the features of the same samples, from their white noise (regenerated: counter-based)
+        F = self._cheap_features(n_samples, sample0)
         Y = t.cat([t.view_as_real(S).reshape(nb * ns, -1), X[:, None]], dim=1)[:n_samples].contiguous()
-        return Y, F[:n_samples].contiguous()
+        return Y, F
 
     def cheap_features(self, n_samples, sample0):
         with self.pl.on_stream():
@@ -75,11 +83,13 @@ class ControlVariate:
         chunk = max(1, pl.ctx.max_batch // nv)
         if self._noise is None:
             self._noise = t.empty(chunk * nv, pl.ng, dtype=t.complex64, device=pl.dev)
-        F = t.empty(n_samples, self.n_feat, dtype=t.float32, device=pl.dev)
+        Fk = t.empty(n_samples, self.n_kfeat, dtype=t.float32, device=pl.dev)
         for s0 in range(0, n_samples, chunk):
             m = min(chunk, n_samples - s0)
             pl.ctx.white_noise(pl.seed, pl.stream_id, sample0 + s0, m, nv, self._noise)
-            pl.ctx.cv_features(self._noise, m, nv, pl.phi, self.m2max, F[s0:s0 + m])
+            pl.ctx.cv_features(self._noise, m, nv, pl.phi, self.m2max, Fk[s0:s0 + m])
+        F = t.empty(n_samples, self.n_feat, dtype=t.float32, device=pl.dev)
+        pl.ctx.cv_shell_sums(Fk, self.m2max, F)
         return F
 
     # -------------------------------------------------------------- network
@@ -88,12 +98,16 @@ class ControlVariate:
             return self._train(F, Y, epochs, batch, lr, holdout)
 
     def _train(self, F, Y, epochs, batch, lr, holdout):
-        """Standardise and fit; the parameters of the epoch with the lowest held-out loss are kept.
-        Returns (training losses, held-out losses)."""
+        """Fit the linear part, then the network on its residuals; the network parameters of the
+        epoch with the lowest held-out loss are kept.  Returns (training losses, held-out losses)."""
         t, ctx = self.torch, self.pl.ctx
         n = F.shape[0]
         nv = max(1, int(round(holdout * n))) if n > 4 else 0
         ntr = n - nv
+        ctx.cv_linear_fit(F[:ntr].contiguous(), Y[:ntr].contiguous(), self.ridge, self.lin)
+        R = t.empty_like(Y)
+        ctx.cv_linear_apply(self.lin, F, self.n_out, R, y=Y)          # residuals Y - f_lin(x)
+        Y = R
         Fs = F.clone()
         ctx.cv_standardize_f32(Fs[:ntr], self.mu_x, self.sd_x, True)
         if nv:
@@ -115,6 +129,14 @@ class ControlVariate:
                     best, best_p = vl, self.mlp.get_params()
         if best_p is not None:
             self.mlp.set_params(best_p)
+        self.use_net = True
+        if nv:
+            # the network is kept only if it beats predicting zero residual on the held-out part
+            p_keep = self.mlp.get_params()
+            self.mlp.set_params(np.zeros_like(p_keep))
+            zero_l, _ = self.mlp.gradients(Fs[ntr:ntr + min(nv, self.max_batch)], T[ntr:ntr + min(nv, self.max_batch)])
+            self.mlp.set_params(p_keep)
+            self.use_net = best < zero_l
         return tr_l, va_l
 
     def predict(self, F):
@@ -144,7 +166,12 @@ class ControlVariate:
         if F_cheap is None:
             self.pl.ctx.cv_rows(None, None, Y_paired, None, None, rows)
         else:
-            self.pl.ctx.cv_rows(self._predict(F_cheap), self._predict(F_paired), Y_paired, self.mu, self.sd, rows)
+            Yl = t.empty_like(Y_paired)          # Y - f_lin(x_paired) + mean f_lin(x_cheap)
+            self.pl.ctx.cv_linear_rows(self.lin, F_cheap.contiguous(), F_paired.contiguous(), Y_paired, Yl)
+            if self.use_net:
+                self.pl.ctx.cv_rows(self._predict(F_cheap), self._predict(F_paired), Yl, self.mu, self.sd, rows)
+            else:
+                rows = Yl
         n = rows.shape[0]
         sig = t.view_as_complex(rows[:, :self.n_sig].contiguous().reshape(n, -1, 2)).contiguous()
         return sig, rows[:, self.n_sig].contiguous()

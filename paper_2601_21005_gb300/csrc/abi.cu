@@ -40,8 +40,9 @@ struct sgw_ctx {
     sgw::KBDev kb;
     double* scal = nullptr;    // small FP64 scratch
     // lazily grown work areas
-    void* work[8] = {nullptr};
-    size_t work_sz[8] = {0};
+    static constexpr int kWorkSlots = 11;
+    void* work[kWorkSlots] = {nullptr};
+    size_t work_sz[kWorkSlots] = {0};
     float2* twM = nullptr;
     int twM_n = 0;
     std::vector<sgw::VecInfo> info_host;
@@ -539,7 +540,7 @@ void sgw_destroy(sgw_ctx* ctx) {
     void* ptrs[] = {ctx->tw, ctx->vloc, ctx->W, ctx->B1, ctx->B2, ctx->info, ctx->scal, ctx->twM};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < sgw_ctx::kWorkSlots; ++i)
         if (ctx->work[i]) cudaFree(ctx->work[i]);
     for (int k = 0; k < SGW_PROF_KINDS; ++k)
         for (auto& pr : ctx->ev_pending[k]) {
@@ -916,7 +917,7 @@ sgw_status sgw_spectral_bounds(sgw_ctx* ctx, int n_iter, uint64_t seed, double m
         }
         for (int it = 0; it < n_iter; ++it) {
             if ((s = sgw_apply_h(ctx, v, w, 1))) return s;
-            Launch L(ctx, SGW_PROF_OTHER, 3);   // memset + two kernels
+            Launch L(ctx, SGW_PROF_OTHER, 2);
             sgw::launch_dot2((int)ctx->ng, v, w, ctx->scal, st);
             CKL();
             sgw::launch_power_update((int)ctx->ng, w, v, ctx->scal, est + pass, pass == 1 ? est : nullptr,
@@ -1294,18 +1295,19 @@ sgw_status sgw_exchange(sgw_ctx* ctx, const void* eta_dev, const float* phi_dev,
     cudaStream_t st = ctx->stream;
     const int64_t ng = ctx->ng;
     const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
-    CK(cudaMemsetAsync(x_dev, 0, sizeof(double) * n_samples, st));
     const int per_call = std::max(1, ctx->max_batch / n_eta);
+    void* wp;
+    if ((s = work(ctx, 10, sizeof(double) * (size_t)sgw::pencil_blocks(ctx->n) * per_call * n_eta, &wp))) return s;
     for (int s0 = 0; s0 < n_samples; s0 += per_call) {
         const int ns = std::min(per_call, n_samples - s0);
         const int B = ns * n_eta;
-        Launch L(ctx, SGW_PROF_OTHER, 3);
+        Launch L(ctx, SGW_PROF_OTHER, 4);
         sgw::launch_scale_mul((int64_t)B * ng, phi_dev, (int)ng, (const float2*)eta_dev + (size_t)s0 * n_eta * ng,
                               ctx->B1, st);
         sgw::launch_plane_fwd(ctx->n, ctx->B1, ctx->W, B, ctx->tw, st);
         // <f|v_C f> = (dV / N) sum_k 4 pi/k^2 |F(k)|^2 ; X = -(1/n_eta) sum_l
         sgw::launch_pencil_coulomb_energy(ctx->n, ctx->W, B, n_eta, kscale, -ctx->dV / (double)ng / n_eta, ctx->tw,
-                                          x_dev + s0, st);
+                                          (double*)wp, x_dev + s0, st);
         CKL();
     }
     return SGW_OK;
@@ -1442,6 +1444,138 @@ sgw_status sgw_cv_rows(sgw_ctx* ctx, const float* f_cheap_dev, int n_cheap, cons
     Launch L(ctx, SGW_PROF_OTHER);
     sgw::launch_cv_rows(n_cheap, n_paired, n_out, f_cheap_dev, f_paired_dev, y_paired_dev, mu_dev, sd_dev, rows_dev,
                         ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+// ---------------------------------------------------------------- control variate: linear part
+static std::vector<int> cv_shell_of_k(int m2max, int* n_shells) {
+    const std::vector<int4> ks = cv_kset(m2max);
+    std::vector<int> sq;
+    for (const int4& k : ks)
+        if (sq.empty() || sq.back() != k.w) sq.push_back(k.w);     // ks is sorted by |m|^2
+    std::vector<int> idx(ks.size());
+    for (size_t i = 0; i < ks.size(); ++i)
+        idx[i] = (int)(std::lower_bound(sq.begin(), sq.end(), ks[i].w) - sq.begin());
+    *n_shells = (int)sq.size();
+    return idx;
+}
+
+int sgw_cv_shell_count(int m2max) {
+    if (m2max < 1) return 2;
+    int ns = 0;
+    cv_shell_of_k(m2max, &ns);
+    return 2 * (ns + 1);
+}
+
+sgw_status sgw_cv_shell_sums(sgw_ctx* ctx, const float* feat_dev, int n_samples, int m2max, float* out_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_samples < 0 || m2max < 1) return fail(ctx, SGW_EINVAL, "bad shell-sum arguments");
+    if (n_samples == 0) return SGW_OK;
+    if (!feat_dev || !out_dev) return fail(ctx, SGW_EINVAL, "null shell-sum pointers");
+    int ns = 0;
+    const std::vector<int> idx = cv_shell_of_k(m2max, &ns);
+    void* p;
+    if ((s = work(ctx, 9, sizeof(int) * idx.size(), &p))) return s;
+    CK(cudaMemcpyAsync(p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));       // idx is a host temporary
+    Launch L(ctx, SGW_PROF_OTHER);
+    sgw::launch_cv_shells(n_samples, (int)idx.size(), ns, (const int*)p, feat_dev, out_dev, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+int64_t sgw_cv_linear_size(int p, int o) { return (p < 1 || o < 1) ? 0 : 2 * (int64_t)p + o + (int64_t)p * o; }
+
+sgw_status sgw_cv_linear_fit(sgw_ctx* ctx, const float* x_dev, const double* y_dev, int n, int p, int o, double ridge,
+                             double* model_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n < 2 || p < 1 || p > 256 || o < 1 || !(ridge >= 0.0) || !x_dev || !y_dev || !model_dev)
+        return fail(ctx, SGW_EINVAL, "bad linear-fit arguments");
+    // work: x in FP64 [n][p], sd of y [o], G [p][p], C [p][o]
+    const size_t nx = (size_t)n * p, ng = (size_t)p * p, nc = (size_t)p * o;
+    void* w;
+    if ((s = work(ctx, 8, sizeof(double) * (nx + o + ng + nc), &w))) return s;
+    double* xd = (double*)w;
+    double* sdy = xd + nx;
+    double* G = sdy + o;
+    double* C = G + ng;
+    double* mu = model_dev;
+    double* sd = model_dev + p;
+    double* ybar = model_dev + 2 * p;
+    double* B = model_dev + 2 * p + o;
+    {
+        Launch L(ctx, SGW_PROF_OTHER, 5);
+        sgw::launch_f32_to_f64((int64_t)nx, x_dev, xd, ctx->stream);
+        sgw::launch_cv_stats(n, p, xd, mu, sd, ctx->stream);
+        sgw::launch_cv_stats(n, o, y_dev, ybar, sdy, ctx->stream);
+        sgw::launch_cv_gram(n, p, xd, mu, sd, G, ctx->stream);
+        sgw::launch_cv_xty(n, p, o, xd, mu, sd, y_dev, ybar, C, ctx->stream);
+        CKL();
+    }
+    // (G + ridge n I) B = C by Cholesky on the host, in FP64
+    std::vector<double> g(ng), c(nc);
+    CK(cudaMemcpyAsync(g.data(), G, sizeof(double) * ng, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(c.data(), C, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int a = 0; a < p; ++a) g[(size_t)a * p + a] += ridge * n;
+    for (int j = 0; j < p; ++j) {
+        double d = g[(size_t)j * p + j];
+        for (int k = 0; k < j; ++k) d -= g[(size_t)j * p + k] * g[(size_t)j * p + k];
+        if (!(d > 0.0)) return fail(ctx, SGW_ENOCONV, "linear fit: normal matrix is not positive definite");
+        const double ljj = std::sqrt(d);
+        g[(size_t)j * p + j] = ljj;
+        for (int i = j + 1; i < p; ++i) {
+            double v = g[(size_t)i * p + j];
+            for (int k = 0; k < j; ++k) v -= g[(size_t)i * p + k] * g[(size_t)j * p + k];
+            g[(size_t)i * p + j] = v / ljj;
+        }
+    }
+    for (int col = 0; col < o; ++col) {
+        std::vector<double> z(p);
+        for (int i = 0; i < p; ++i) {
+            double v = c[(size_t)i * o + col];
+            for (int k = 0; k < i; ++k) v -= g[(size_t)i * p + k] * z[k];
+            z[i] = v / g[(size_t)i * p + i];
+        }
+        for (int i = p - 1; i >= 0; --i) {
+            double v = z[i];
+            for (int k = i + 1; k < p; ++k) v -= g[(size_t)k * p + i] * c[(size_t)k * o + col];
+            c[(size_t)i * o + col] = v / g[(size_t)i * p + i];
+        }
+    }
+    CK(cudaMemcpyAsync(B, c.data(), sizeof(double) * nc, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SGW_OK;
+}
+
+sgw_status sgw_cv_linear_apply(sgw_ctx* ctx, const double* model_dev, const float* x_dev, int n, int p, int o,
+                               const double* y_dev, double* out_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n < 0 || p < 1 || o < 1 || !model_dev || (n > 0 && (!x_dev || !out_dev)))
+        return fail(ctx, SGW_EINVAL, "bad linear-apply arguments");
+    Launch L(ctx, SGW_PROF_OTHER);
+    sgw::launch_cv_lin_apply(n, p, o, model_dev, x_dev, y_dev, out_dev, ctx->stream);
+    CKL();
+    return SGW_OK;
+}
+
+sgw_status sgw_cv_linear_rows(sgw_ctx* ctx, const double* model_dev, const float* x_cheap_dev, int n_cheap,
+                              const float* x_paired_dev, int n_paired, int p, int o, const double* y_dev,
+                              double* y_out_dev) {
+    sgw_status s = check_ctx(ctx, false);
+    if (s) return s;
+    if (n_cheap < 1 || n_paired < 1 || p < 1 || o < 1 || !model_dev || !x_cheap_dev || !x_paired_dev || !y_dev ||
+        !y_out_dev)
+        return fail(ctx, SGW_EINVAL, "bad linear-rows arguments");
+    void* w;
+    if ((s = work(ctx, 9, sizeof(double) * std::max(p, 64), &w))) return s;
+    Launch L(ctx, SGW_PROF_OTHER, 2);
+    sgw::launch_cv_lin_rows(n_cheap, n_paired, p, o, model_dev, x_cheap_dev, x_paired_dev, y_dev, (double*)w,
+                            y_out_dev, ctx->stream);
     CKL();
     return SGW_OK;
 }

@@ -256,8 +256,7 @@ k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restr
 // acc[b / per] += dvn * sum_k 4 pi / k^2 |F(k)|^2 (FP64).
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::PENCIL_NT)
-k_pencil_energy(const float2* __restrict__ W, int per, float kscale, double dvn, const float2* __restrict__ tw,
-                double* __restrict__ acc) {
+k_pencil_energy(const float2* __restrict__ W, float kscale, const float2* __restrict__ tw, double* __restrict__ part) {
     extern __shared__ float2 sm[];
     __shared__ double red[32];
     constexpr int NT = Cfg<N>::PENCIL_NT, TX = Cfg<N>::TX, NXT = N / TX;
@@ -291,7 +290,27 @@ k_pencil_energy(const float2* __restrict__ W, int per, float kscale, double dvn,
     if (threadIdx.x < 32) {
         double t = threadIdx.x < NT / 32 ? red[threadIdx.x] : 0.0;
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) atomicAdd(acc + blockIdx.y / per, t * dvn);
+        if (threadIdx.x == 0) part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// acc[s] = dvn * sum of the partials of vectors s*per .. s*per+per-1 (fixed order: one block per
+// sample, a strided pass then a shuffle tree)
+__global__ void __launch_bounds__(256)
+k_energy_reduce(const double* __restrict__ part, int per, int nblk, double dvn, double* __restrict__ acc) {
+    __shared__ double red[8];
+    const int s = blockIdx.x;
+    const int64_t total = (int64_t)per * nblk;
+    const double* p = part + (size_t)s * total;
+    double t = 0.0;
+    for (int64_t i = threadIdx.x; i < total; i += blockDim.x) t += p[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double u = threadIdx.x < 8 ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) u += __shfl_xor_sync(0xffffffffu, u, o);
+        if (threadIdx.x == 0) acc[s] = u * dvn;
     }
 }
 
@@ -664,11 +683,15 @@ void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ec
     });
 }
 
+int pencil_blocks(int n) { return (n / 16) * n; }
+
 void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
-                                  const float2* tw, double* acc, cudaStream_t st) {
+                                  const float2* tw, double* part, double* acc, cudaStream_t st) {
     SGW_DISPATCH_N(n, {
+        static_assert(Cfg<N>::TX == 16, "pencil_blocks assumes 16-column tiles");
         const dim3 grid((N / Cfg<N>::TX) * N, batch);
-        k_pencil_energy<N><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, per, kscale, dvn, tw, acc);
+        k_pencil_energy<N><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, tw, part);
+        k_energy_reduce<<<batch / per, 256, 0, st>>>(part, per, (int)grid.x, dvn, acc);
     });
 }
 

@@ -178,9 +178,10 @@ __device__ __forceinline__ void block_sumf(float (&v)[NV], float* sh /*[32*NV]*/
 }
 
 // ------------------------------------------------------------------ power iteration (Sec. 2.1)
-// scal[0] += Re <v|w>/dV, scal[1] += <w|w>/dV, scal[2] += <v|v>/dV  (the dV factors cancel)
-__global__ void __launch_bounds__(256) k_dot2(int64_t ng, const float2* __restrict__ v, const float2* __restrict__ w,
-                                              double* scal) {
+// scal[0] = Re <v|w>/dV, scal[1] = <w|w>/dV, scal[2] = <v|v>/dV  (the dV factors cancel).  One
+// block, so that the sums have a fixed order (the iteration runs once per setup).
+__global__ void __launch_bounds__(1024) k_dot2(int64_t ng, const float2* __restrict__ v, const float2* __restrict__ w,
+                                               double* scal) {
     __shared__ double sh[32 * 3];
     double a[3] = {0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ng; i += (int64_t)gridDim.x * blockDim.x) {
@@ -191,16 +192,14 @@ __global__ void __launch_bounds__(256) k_dot2(int64_t ng, const float2* __restri
     }
     block_sum<3>(a, sh);
     if (threadIdx.x == 0) {
-        atomicAdd(scal + 0, a[0]);
-        atomicAdd(scal + 1, a[1]);
-        atomicAdd(scal + 2, a[2]);
+        scal[0] = a[0];
+        scal[1] = a[1];
+        scal[2] = a[2];
     }
 }
 
 void launch_dot2(int ng, const float2* v, const float2* w, double* scal, cudaStream_t st) {
-    cudaMemsetAsync(scal, 0, 3 * sizeof(double), st);
-    const int blocks = std::min<int>((ng + 255) / 256, 152 * 4);
-    k_dot2<<<blocks, 256, 0, st>>>(ng, v, w, scal);
+    k_dot2<<<1, 1024, 0, st>>>(ng, v, w, scal);
 }
 
 // With sigma = *shift (0 if null): est = (S0 - sigma S2)/S2 (Rayleigh quotient of A = H - sigma);

@@ -7,6 +7,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -163,8 +164,16 @@ __global__ void k_loss_grad(int64_t n, int O, const float* __restrict__ y, const
     if (threadIdx.x < 32) {
         double s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (threadIdx.x == 0) atomicAdd(loss, s);
+        if (threadIdx.x == 0) loss[1 + blockIdx.x] = s;      // per-block partial, summed by k_loss_sum
     }
+}
+
+// loss[0] = sum of the nb per-block partials loss[1 .. nb] in a fixed order (one warp)
+__global__ void k_loss_sum(int nb, double* loss) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += 32) s += loss[1 + i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) loss[0] = s;
 }
 
 // db[n] = sum_m d[m][n]   (one thread per column, fixed order)
@@ -320,6 +329,100 @@ __global__ void k_cv_rows(int Mc, int n, int O, const float* __restrict__ fc, co
 
 // ================================================================== host side
 namespace sgw {
+// ---------------------------------------------------------------- shell sums and the linear part
+// out[i][c]: c < S: sum of the zeta-bar features of shell c, c = S: the zeta-bar k = 0 feature,
+// then the same for the eta-bar block (S = n_shells); fixed k order, FP64 accumulation.
+__global__ void k_cv_shells(int n, int nk, int n_shells, const int* __restrict__ shell_of_k,
+                            const float* __restrict__ feat, float* __restrict__ out) {
+    const int per = 2 * (n_shells + 1);
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * per) return;
+    const int i = t / per, c = t % per, half = c / (n_shells + 1), sh = c % (n_shells + 1);
+    const float* f = feat + (size_t)i * 2 * (nk + 1) + (size_t)half * (nk + 1);
+    double acc = 0.0;
+    if (sh == n_shells) {
+        acc = f[nk];
+    } else {
+        for (int k = 0; k < nk; ++k)
+            if (__ldg(shell_of_k + k) == sh) acc += f[k];
+    }
+    out[t] = (float)acc;
+}
+
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
+
+// G[a][b] = sum_r xs[r][a] xs[r][b], xs = (x - mu) / sd  (rows in increasing order)
+__global__ void k_cv_gram(int n, int p, const double* __restrict__ x, const double* __restrict__ mu,
+                          const double* __restrict__ sd, double* __restrict__ G) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= p * p) return;
+    const int a = t / p, b = t % p;
+    double acc = 0.0;
+    for (int r = 0; r < n; ++r)
+        acc += ((x[(size_t)r * p + a] - mu[a]) / sd[a]) * ((x[(size_t)r * p + b] - mu[b]) / sd[b]);
+    G[t] = acc;
+}
+
+// C[a][j] = sum_r xs[r][a] (y[r][j] - ybar[j])
+__global__ void k_cv_xty(int n, int p, int o, const double* __restrict__ x, const double* __restrict__ mu,
+                         const double* __restrict__ sd, const double* __restrict__ y, const double* __restrict__ ybar,
+                         double* __restrict__ C) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)p * o) return;
+    const int a = (int)(t / o), j = (int)(t % o);
+    double acc = 0.0;
+    for (int r = 0; r < n; ++r) acc += ((x[(size_t)r * p + a] - mu[a]) / sd[a]) * (y[(size_t)r * o + j] - ybar[j]);
+    C[t] = acc;
+}
+
+// Linear model m = [mu p][sd p][ybar o][B p x o]; f(x)_j = ybar_j + sum_a ((x_a - mu_a) / sd_a) B_aj
+__device__ __forceinline__ double lin_eval(const double* __restrict__ m, int p, int o, const float* x, int j) {
+    const double* mu = m;
+    const double* sd = m + p;
+    const double* ybar = m + 2 * p;
+    const double* B = m + 2 * p + o;
+    double acc = ybar[j];
+    for (int a = 0; a < p; ++a) acc += (((double)x[a] - mu[a]) / sd[a]) * B[(size_t)a * o + j];
+    return acc;
+}
+
+// out = f(x), or y - f(x) when y is given
+__global__ void k_cv_lin_apply(int n, int p, int o, const double* __restrict__ m, const float* __restrict__ x,
+                               const double* __restrict__ y, double* __restrict__ out) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * o) return;
+    const int i = (int)(t / o), j = (int)(t % o);
+    const double f = lin_eval(m, p, o, x + (size_t)i * p, j);
+    out[t] = y != nullptr ? y[t] - f : f;
+}
+
+// xbar[a] = mean over the m cheap samples of x[.][a] (fixed order)
+__global__ void k_cv_lin_mean(int mc, int p, const float* __restrict__ x, double* __restrict__ xbar) {
+    const int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a >= p) return;
+    double acc = 0.0;
+    for (int r = 0; r < mc; ++r) acc += (double)x[(size_t)r * p + a];
+    xbar[a] = acc / mc;
+}
+
+// yout[i][j] = y[i][j] - f(x_i)_j + f(xbar)_j  (the mean of a linear f over the cheap samples)
+__global__ void k_cv_lin_rows(int n, int p, int o, const double* __restrict__ m, const double* __restrict__ xbar,
+                              const float* __restrict__ xp, const double* __restrict__ y, double* __restrict__ yout) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * o) return;
+    const int i = (int)(t / o), j = (int)(t % o);
+    const double* mu = m;
+    const double* sd = m + p;
+    const double* B = m + 2 * p + o;
+    double d = 0.0;     // f(x_i) - f(xbar) = sum_a (x_ia - xbar_a) / sd_a B_aj
+    for (int a = 0; a < p; ++a) d += (((double)xp[(size_t)i * p + a] - mu[a]) / sd[a] - (xbar[a] - mu[a]) / sd[a]) *
+                                     B[(size_t)a * o + j];
+    yout[t] = y[t] - d;
+}
+
 void launch_cv_source(int64_t ng, const float2* zb, int64_t stride, const float* phi, int n_samples, float2* out,
                       cudaStream_t st) {
     const int64_t total = ng * n_samples;
@@ -356,6 +459,39 @@ void launch_cv_rows(int Mc, int n, int O, const float* fc, const float* fp, cons
                     const double* sd, double* rows, cudaStream_t st) {
     k_cv_rows<<<(O + 127) / 128, 128, 0, st>>>(Mc, n, O, fc, fp, y, mu, sd, rows);
 }
+
+void launch_cv_shells(int n, int nk, int n_shells, const int* shell_of_k, const float* feat, float* out, cudaStream_t st) {
+    const int total = n * 2 * (n_shells + 1);
+    if (total > 0) k_cv_shells<<<(total + 127) / 128, 128, 0, st>>>(n, nk, n_shells, shell_of_k, feat, out);
+}
+
+void launch_f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t st) {
+    if (n > 0) k_f32_to_f64<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(n, a, b);
+}
+
+void launch_cv_gram(int n, int p, const double* x, const double* mu, const double* sd, double* G, cudaStream_t st) {
+    k_cv_gram<<<(p * p + 127) / 128, 128, 0, st>>>(n, p, x, mu, sd, G);
+}
+
+void launch_cv_xty(int n, int p, int o, const double* x, const double* mu, const double* sd, const double* y,
+                   const double* ybar, double* C, cudaStream_t st) {
+    const int64_t total = (int64_t)p * o;
+    k_cv_xty<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(n, p, o, x, mu, sd, y, ybar, C);
+}
+
+void launch_cv_lin_apply(int n, int p, int o, const double* m, const float* x, const double* y, double* out,
+                         cudaStream_t st) {
+    const int64_t total = (int64_t)n * o;
+    if (total > 0) k_cv_lin_apply<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(n, p, o, m, x, y, out);
+}
+
+void launch_cv_lin_rows(int mc, int n, int p, int o, const double* m, const float* xc, const float* xp,
+                        const double* y, double* xbar, double* yout, cudaStream_t st) {
+    k_cv_lin_mean<<<(p + 63) / 64, 64, 0, st>>>(mc, p, xc, xbar);
+    const int64_t total = (int64_t)n * o;
+    if (total > 0) k_cv_lin_rows<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(n, p, o, m, xbar, xp, y, yout);
+}
+
 }  // namespace sgw
 
 struct sgw_mlp {
@@ -418,9 +554,9 @@ sgw_status mlp_forward(sgw_mlp* m, const float* x, int M) {
 sgw_status mlp_backward(sgw_mlp* m, const float* t, int M) {
     cudaStream_t st = m->stream;
     const int H = m->width, I = m->n_in, O = m->n_out;
-    MCK(cudaMemsetAsync(m->loss, 0, sizeof(double), st));
     const int64_t ny = (int64_t)M * O;
     sgw::k_loss_grad<<<grid1(ny), 256, 0, st>>>(ny, O, m->Y, t, m->lw, 2.0f / (float)ny, m->dY, m->dYbf, m->loss);
+    sgw::k_loss_sum<<<1, 32, 0, st>>>((int)grid1(ny), m->loss);
     // layer 4
     {
         sgw::GemmEpi ep{sgw::EPI_STORE, nullptr, m->G + m->woff[3], O, nullptr, nullptr};
@@ -479,7 +615,7 @@ sgw_status sgw_mlp_create(sgw_mlp** out, int n_in, int width, int n_out, int max
               cudaMalloc(&m->Ma, 4 * off) == cudaSuccess && cudaMalloc(&m->Va, 4 * off) == cudaSuccess &&
               cudaMalloc(&m->Pbf, 2 * off) == cudaSuccess && cudaMalloc(&m->Xbf, 2 * B * n_in) == cudaSuccess &&
               cudaMalloc(&m->Y, 4 * B * n_out) == cudaSuccess && cudaMalloc(&m->dY, 4 * B * n_out) == cudaSuccess &&
-              cudaMalloc(&m->dYbf, 2 * B * n_out) == cudaSuccess && cudaMalloc(&m->loss, 8) == cudaSuccess;
+              cudaMalloc(&m->dYbf, 2 * B * n_out) == cudaSuccess && cudaMalloc(&m->loss, sizeof(double) * (1 + 152 * 16)) == cudaSuccess;
     for (int l = 0; l < 3 && ok; ++l)
         ok = cudaMalloc(&m->Abf[l], 2 * B * width) == cudaSuccess && cudaMalloc(&m->Z[l], 4 * B * width) == cudaSuccess;
     for (int l = 0; l < 2 && ok; ++l)

@@ -98,8 +98,9 @@ void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float
 void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw,
                    cudaStream_t st, int pf_ahead = 0);
 // exchange energy: acc[b / per] += (dV / N) sum_k v(k) |F(k)|^2 after the z transform
+int pencil_blocks(int n);
 void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
-                                  const float2* tw, double* acc, cudaStream_t st);
+                                  const float2* tw, double* part, double* acc, cudaStream_t st);
 void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant = 0);
 // inverse xy transform of W, epilogue: mode 0 -> out_c[b] = plane (c64);
 // mode 1 (Poisson of TDH densities) -> vtot[b] = vloc + Re, dv[b] = Im, uR[b] = Im (if uR)
@@ -149,6 +150,15 @@ void launch_cv_combine(int n_samples, int nv, int nk, const float* raw, float* f
 void launch_cv_standardize_f32(int n, int O, float* y, double* mu, double* sd, int compute, cudaStream_t st);
 void launch_cv_standardize(int64_t total, int O, const double* y, const double* mu, const double* sd, float* t,
                            cudaStream_t st);
+void launch_cv_shells(int n, int nk, int n_shells, const int* shell_of_k, const float* feat, float* out, cudaStream_t st);
+void launch_f32_to_f64(int64_t n, const float* a, double* b, cudaStream_t st);
+void launch_cv_gram(int n, int p, const double* x, const double* mu, const double* sd, double* G, cudaStream_t st);
+void launch_cv_xty(int n, int p, int o, const double* x, const double* mu, const double* sd, const double* y,
+                   const double* ybar, double* C, cudaStream_t st);
+void launch_cv_lin_apply(int n, int p, int o, const double* m, const float* x, const double* y, double* out,
+                         cudaStream_t st);
+void launch_cv_lin_rows(int mc, int n, int p, int o, const double* m, const float* xc, const float* xp,
+                        const double* y, double* xbar, double* yout, cudaStream_t st);
 void launch_cv_rows(int Mc, int n, int O, const float* fc, const float* fp, const double* y, const double* mu,
                     const double* sd, double* rows, cudaStream_t st);
 void launch_prepare(int ng, const float2* noise, const float2* filt, const float* phi, int n_samples, int n_eta,

@@ -19,7 +19,7 @@ class Pipeline:
     def __init__(self, n, h, vloc, kb_atoms, phi, e_homo, e_lumo, n_eta=8, n_steps=200, dt=0.05,
                  cheb_deg=16, n_cheb=128, samples_per_batch=1, seed=1000, stream_id=1, device=0, ecut=0.0,
                  spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None, graphs=False,
-                 autotune=False):
+                 autotune=False, zeta_group=1):
         import torch
         self.torch = torch
         # CUDA graphs need a non-default stream: the pipeline then owns one, and its buffers are
@@ -29,11 +29,19 @@ class Pipeline:
             stream = self.stream.cuda_stream
         self.n, self.h, self.ng = n, h, n ** 3
         self.n_eta, self.n_steps, self.dt, self.cheb_deg = n_eta, n_steps, dt, cheb_deg
+        # a run is zeta_group chunks of samples_per_batch samples: white noise, filter, exchange, TDH and
+        # time ordering chunk by chunk (2 N_eta samples_per_batch TDH orbitals per launch), then the
+        # zeta pairs of all the run's samples in one propagation (2 samples_per_batch zeta_group
+        # vectors per launch), with u of every sample of the run kept in HBM
         self.ns = samples_per_batch
+        self.group = int(zeta_group)
+        if self.group < 1:
+            raise ValueError('zeta_group must be >= 1')
+        self.run_samples = self.ns * self.group
         self.seed, self.stream_id = seed, stream_id
         self.fp64 = 1 if fp64 else 0
         self.dev = torch.device('cuda', device)
-        mb = max(self.ns * (n_eta + 1), 2 * self.ns * n_eta, 2 * self.ns)
+        mb = max(self.ns * (n_eta + 1), 2 * self.ns * n_eta, 2 * self.run_samples)
         self.ctx = _sgw.Context(n, h, ecut=ecut, max_batch=mb, device=device, stream=stream)
         if graphs:
             self.ctx.set_graph_mode(True)
@@ -56,10 +64,10 @@ class Pipeline:
         self.noise = torch.empty(ns * (n_eta + 1), ng, dtype=c64, device=self.dev)
         self.filt = torch.empty_like(self.noise)
         self.eta = torch.empty(ns * n_eta, ng, dtype=c64, device=self.dev)
-        self.zeta = torch.empty(2 * ns, ng, dtype=c64, device=self.dev)
+        self.zeta = torch.empty(2 * self.run_samples, ng, dtype=c64, device=self.dev)
         self.source = torch.empty(ns, ng, dtype=f32, device=self.dev)
         self.uR = torch.empty(ns, N + 1, ng, dtype=f32, device=self.dev)
-        self.u = torch.empty(ns, N + 1, ng, dtype=c64, device=self.dev)
+        self.u = torch.empty(self.run_samples, N + 1, ng, dtype=c64, device=self.dev)
 
     @contextlib.contextmanager
     def on_stream(self):
@@ -80,29 +88,34 @@ class Pipeline:
         return 3.0 / (self.n_steps * self.dt)
 
     def run_batch(self, sample0, sigma_out, x_out):
-        """Samples sample0 .. sample0 + ns - 1; writes Sigma_i(t) [ns][2N+1] (complex128) and X_i [ns]."""
+        """Samples sample0 .. sample0 + run_samples - 1; writes Sigma_i(t) [run_samples][2N+1]
+        (complex128) and X_i [run_samples]."""
         with self.on_stream():
             self._run_batch(sample0, sigma_out, x_out)
 
     def _run_batch(self, sample0, sigma_out, x_out):
         c, ns, ne, N = self.ctx, self.ns, self.n_eta, self.n_steps
-        c.white_noise(self.seed, self.stream_id, sample0, ns, ne + 1, self.noise)
-        c.filter_occupied(self.coeffs, self.noise, self.filt)
-        c.prepare_sample(self.noise, self.filt, self.phi, ns, ne, self.eta, self.zeta, self.source)
-        c.exchange(self.eta, self.phi, ns, ne, x_out)
-        c.tdh_response(self.eta, self.source, ns, ne, N, self.dt, self.cheb_deg, self.uR)
-        c.time_order(self.uR, self.u, ns, N)
-        c.sigma_c(self.zeta, self.phi, self.u, ns, N, self.dt, self.cheb_deg, sigma_out, self.fp64)
+        for g in range(self.group):
+            s0 = g * ns
+            c.white_noise(self.seed, self.stream_id, sample0 + s0, ns, ne + 1, self.noise)
+            c.filter_occupied(self.coeffs, self.noise, self.filt)
+            c.prepare_sample(self.noise, self.filt, self.phi, ns, ne, self.eta, self.zeta[2 * s0:2 * (s0 + ns)],
+                             self.source)
+            c.exchange(self.eta, self.phi, ns, ne, x_out[s0:s0 + ns])
+            c.tdh_response(self.eta, self.source, ns, ne, N, self.dt, self.cheb_deg, self.uR)
+            c.time_order(self.uR, self.u[s0:s0 + ns], ns, N)
+        c.sigma_c(self.zeta, self.phi, self.u, self.run_samples, N, self.dt, self.cheb_deg, sigma_out, self.fp64)
 
     def run(self, n_samples, sample0=0):
-        """Run n_samples (a multiple of the batch size); returns device Sigma [n][2N+1] and X [n]."""
+        """Run n_samples (rounded up to whole runs); returns device Sigma [n][2N+1] and X [n]."""
         t = self.torch
-        nb = (n_samples + self.ns - 1) // self.ns
-        sig = t.empty(nb * self.ns, 2 * self.n_steps + 1, dtype=t.complex128, device=self.dev)
-        xs = t.empty(nb * self.ns, dtype=t.float64, device=self.dev)
+        rs = self.run_samples
+        nb = (n_samples + rs - 1) // rs
+        sig = t.empty(nb * rs, 2 * self.n_steps + 1, dtype=t.complex128, device=self.dev)
+        xs = t.empty(nb * rs, dtype=t.float64, device=self.dev)
         for b in range(nb):
-            s0 = b * self.ns
-            self.run_batch(sample0 + s0, sig[s0:s0 + self.ns], xs[s0:s0 + self.ns])
+            s0 = b * rs
+            self.run_batch(sample0 + s0, sig[s0:s0 + rs], xs[s0:s0 + rs])
         return sig[:n_samples], xs[:n_samples]
 
     def qp(self, sigma, x, eps_ks, vxc=0.0, window=2.0, step=1e-3, fp64=None):

@@ -58,6 +58,12 @@ _SIGS = {
     'sgw_cv_standardize': ([_P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P], _c.c_int),
     'sgw_cv_standardize_f32': ([_P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P], _c.c_int),
     'sgw_cv_rows': ([_P, _P, _c.c_int, _P, _P, _c.c_int, _c.c_int, _P, _P, _P], _c.c_int),
+    'sgw_cv_shell_count': ([_c.c_int], _c.c_int),
+    'sgw_cv_shell_sums': ([_P, _P, _c.c_int, _c.c_int, _P], _c.c_int),
+    'sgw_cv_linear_size': ([_c.c_int, _c.c_int], _c.c_int64),
+    'sgw_cv_linear_fit': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _P], _c.c_int),
+    'sgw_cv_linear_apply': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P], _c.c_int),
+    'sgw_cv_linear_rows': ([_P, _P, _P, _c.c_int, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P], _c.c_int),
     'sgw_mlp_create': ([_c.POINTER(_P), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64, _c.c_int, _P], _c.c_int),
     'sgw_mlp_destroy': ([_P], None),
     'sgw_mlp_last_error': ([_P], _c.c_char_p),
@@ -164,6 +170,14 @@ def sgw_qp_energy_noalloc(sigma, x, n_samples, n_steps, dt, gamma, eps_ks, vxc=0
 
 def sgw_cv_feature_count(m2max):
     return lib().sgw_cv_feature_count(m2max)
+
+
+def sgw_cv_shell_count(m2max):
+    return lib().sgw_cv_shell_count(m2max)
+
+
+def sgw_cv_linear_size(p, o):
+    return lib().sgw_cv_linear_size(p, o)
 
 
 class MLP:
@@ -423,6 +437,32 @@ class Context:
                                                                        x.shape[1], 1 if compute_stats else 0,
                                                                        _dev(mu, torch.float64),
                                                                        _dev(sd, torch.float64)))
+
+    def cv_shell_sums(self, feat, m2max, out):
+        import torch
+        self._ck('sgw_cv_shell_sums', lib().sgw_cv_shell_sums(self._p, _dev(feat, torch.float32), feat.shape[0], m2max,
+                                                             _dev(out, torch.float32)))
+
+    def cv_linear_fit(self, x, y, ridge, model):
+        import torch
+        self._ck('sgw_cv_linear_fit', lib().sgw_cv_linear_fit(self._p, _dev(x, torch.float32), _dev(y, torch.float64),
+                                                             x.shape[0], x.shape[1], y.shape[1], float(ridge),
+                                                             _dev(model, torch.float64)))
+
+    def cv_linear_apply(self, model, x, o, out, y=None):
+        """out = f(x), or y - f(x) when y is given."""
+        import torch
+        self._ck('sgw_cv_linear_apply', lib().sgw_cv_linear_apply(self._p, _dev(model, torch.float64),
+                                                                 _dev(x, torch.float32), x.shape[0], x.shape[1], o,
+                                                                 _dev(y, torch.float64), _dev(out, torch.float64)))
+
+    def cv_linear_rows(self, model, x_cheap, x_paired, y, y_out):
+        import torch
+        self._ck('sgw_cv_linear_rows', lib().sgw_cv_linear_rows(self._p, _dev(model, torch.float64),
+                                                               _dev(x_cheap, torch.float32), x_cheap.shape[0],
+                                                               _dev(x_paired, torch.float32), x_paired.shape[0],
+                                                               x_paired.shape[1], y.shape[1], _dev(y, torch.float64),
+                                                               _dev(y_out, torch.float64)))
 
     def cv_rows(self, f_cheap, f_paired, y_paired, mu, sd, rows):
         import torch

@@ -188,3 +188,45 @@ def test_control_variate_gain_tiny():
     # no cheap samples: the rows are the plain samples, bit for bit
     S2, X2 = cv.rows(None, None, Yp)
     assert torch.equal(S2, S0) and torch.equal(X2, X0)
+
+
+def test_cv_shell_sums_and_linear_part_match_oracle():
+    sg = _sgw()
+    s = synth.wells()
+    ctx = sg.Context(s['n'], s['h'], max_batch=2)
+    rng = np.random.default_rng(12)
+    m2 = 10
+    nk, ns = sg.sgw_cv_feature_count(m2), sg.sgw_cv_shell_count(m2)
+    assert ns == omlp.shell_count(m2)
+    fk = rng.random(size=(9, nk)).astype(np.float32)
+    out = torch.empty(9, ns, dtype=torch.float32, device='cuda')
+    ctx.cv_shell_sums(gc.to_dev(fk, torch, torch.float32), m2, out)
+    assert np.allclose(out.cpu().numpy(), omlp.shell_sums(fk.astype(np.float64), m2), rtol=1e-6)
+    # ridge fit, prediction, residuals and rows against the FP64 oracle on the same float inputs
+    n, p, o, mc = 57, ns, 13, 40
+    x = (rng.normal(size=(n, p)) * rng.uniform(0.1, 10, size=p) + rng.normal(size=p)).astype(np.float32)
+    y = x.astype(np.float64) @ rng.normal(size=(p, o)) + 0.3 * rng.normal(size=(n, o))
+    xd, yd = gc.to_dev(x, torch, torch.float32), gc.to_dev(y, torch, torch.float64)
+    model = torch.zeros(sg.sgw_cv_linear_size(p, o), dtype=torch.float64, device='cuda')
+    ctx.cv_linear_fit(xd, yd, 1e-3, model)
+    mu, sd, ybar, B = omlp.linear_fit(x.astype(np.float64), y, 1e-3)
+    m = model.cpu().numpy()
+    assert np.allclose(m[:p], mu, rtol=1e-12) and np.allclose(m[p:2 * p], sd, rtol=1e-12)
+    assert np.allclose(m[2 * p:2 * p + o], ybar, rtol=1e-12)
+    assert np.max(np.abs(m[2 * p + o:].reshape(p, o) - B)) < 1e-9 * np.max(np.abs(B))
+    f = torch.empty(n, o, dtype=torch.float64, device='cuda')
+    ctx.cv_linear_apply(model, xd, o, f)
+    ref = omlp.linear_apply((mu, sd, ybar, B), x.astype(np.float64))
+    assert np.max(np.abs(f.cpu().numpy() - ref)) < 1e-9 * np.max(np.abs(ref))
+    r = torch.empty_like(f)
+    ctx.cv_linear_apply(model, xd, o, r, y=yd)
+    assert np.max(np.abs(r.cpu().numpy() - (y - ref))) < 1e-9 * np.max(np.abs(ref))
+    xc = rng.normal(size=(mc, p)).astype(np.float32) * x.std(0) + x.mean(0)
+    rows = torch.empty_like(yd)
+    ctx.cv_linear_rows(model, gc.to_dev(xc, torch, torch.float32), xd, yd, rows)
+    model_np = (mu, sd, ybar, B)
+    want = omlp.cv_rows(omlp.linear_apply(model_np, xc.astype(np.float64)), ref, y)
+    assert np.max(np.abs(rows.cpu().numpy() - want)) < 1e-9 * np.max(np.abs(want))
+    # a fit needs at least two samples
+    with pytest.raises(RuntimeError):
+        ctx.cv_linear_fit(xd[:1], yd[:1], 1e-3, model)

@@ -84,3 +84,20 @@ def test_graphs_speed_up_the_tiny_pipeline():
     print('tiny pipeline per sample: direct %.1f ms, graphs %.1f ms' % (1e3 * times[False], 1e3 * times[True]))
     assert torch.equal(res[False], res[True])
     assert times[True] < times[False]
+
+
+def test_grouped_zeta_runs_match_single_chunks():
+    """A run of 3 chunks whose zeta pairs propagate together gives, sample by sample, the same bits
+    as three separate one-chunk runs (per-vector arithmetic does not depend on the batch)."""
+    from paper_2601_21005_gb300.pipeline import Pipeline
+    s = synth.wells()
+    g, kb, w, phis = gc.oracle_eigs(s, 8)
+    kw = dict(n_eta=4, n_steps=20, dt=0.05, cheb_deg=16, n_cheb=64, samples_per_batch=2, seed=21,
+              spectrum=(-4.0, 45.0))
+    one = Pipeline(s['n'], s['h'], s['vloc'], [], phis[3], w[3], w[4], zeta_group=1, **kw)
+    grp = Pipeline(s['n'], s['h'], s['vloc'], [], phis[3], w[3], w[4], zeta_group=3, **kw)
+    assert grp.run_samples == 6 and one.run_samples == 2
+    s1, x1 = one.run(6, sample0=40)
+    s3, x3 = grp.run(6, sample0=40)
+    torch.cuda.synchronize()
+    assert torch.equal(s1, s3) and torch.equal(x1, x3)
