@@ -22,16 +22,19 @@ def main():
     ap.add_argument('--steps', type=int, default=2)
     ap.add_argument('--deg', type=int, default=16)
     ap.add_argument('--no-kb', action='store_true')
+    ap.add_argument('--radius', type=float, default=None,
+                    help='cluster radius in bohr (default 10.5 = Si35H36; 28.0 = Si657H300 at n = 128)')
     ap.add_argument('--tune', default=None,
                     help='semicolon-separated settings "operands,plane_lookahead,pencil_lookahead" to time in turn')
     ap.add_argument('--autotune', action='store_true', help='run the library autotuner first and report its choice')
     args = ap.parse_args()
     build.build()
-    s = synth.si_cluster(n=args.n, h=0.5, radius=10.5 if args.n >= 64 else 4.5)
+    radius = args.radius if args.radius is not None else (10.5 if args.n >= 64 else 4.5)
+    s = synth.si_cluster(n=args.n, h=0.5, radius=radius)
     ctx = sgw.Context(args.n, 0.5, max_batch=args.batch)
     ctx.set_potential(torch.as_tensor(s['vloc'].reshape(-1).astype(np.float32)).cuda(),
                       [] if args.no_kb else s['kb_atoms'])
-    ctx.set_spectrum(-3.2, 62.2)
+    ctx.set_spectrum(float(s['vloc'].min()) - 1.0, 0.5 * 3 * (np.pi / 0.5) ** 2 + 3.0)
     ng = args.n ** 3
     psi = torch.empty(args.batch, ng, dtype=torch.complex64, device='cuda')
     ctx.white_noise(5, 3, 0, 1, args.batch, psi)

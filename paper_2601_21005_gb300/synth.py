@@ -38,15 +38,32 @@ def min_image(d, L):
 
 
 def gaussian_wells_potential(n, h, centers, depths, widths):
-    """V(r) = -sum_a D_a exp(-|r - R_a|^2 / (2 w_a^2)) with minimum-image distances."""
+    """V(r) = -sum_a D_a exp(-|r - R_a|^2 / (2 w_a^2)) with minimum-image distances.
+
+    Each Gaussian is evaluated where it exceeds exp(-37) of its depth (|r - R_a| <= sqrt(74) w_a),
+    on a periodic box around R_a when that box is shorter than the cell, else on the whole grid."""
     L = n * h
-    Z, Y, X = grid_coords(n, h)
     v = np.zeros((n, n, n))
+    Z = Y = X = None
     for (cx, cy, cz), d, w in zip(centers, depths, widths):
-        dx = min_image(X - cx, L)
-        dy = min_image(Y - cy, L)
-        dz = min_image(Z - cz, L)
-        v -= d * np.exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * w * w))
+        rc = np.sqrt(74.0) * w
+        if 2.0 * rc + 2.0 * h < L:
+            c = np.array([cx, cy, cz])
+            lo = np.floor((c - rc) / h).astype(int)
+            hi = np.ceil((c + rc) / h).astype(int)
+            ix, iy, iz = (np.arange(lo[k], hi[k] + 1) for k in range(3))
+            dx = ix * h - cx
+            dy = iy * h - cy
+            dz = iz * h - cz
+            g = np.exp(-(dz[:, None, None] ** 2 + dy[None, :, None] ** 2 + dx[None, None, :] ** 2) / (2.0 * w * w))
+            v[np.ix_(iz % n, iy % n, ix % n)] -= d * g
+        else:
+            if Z is None:
+                Z, Y, X = grid_coords(n, h)
+            dx = min_image(X - cx, L)
+            dy = min_image(Y - cy, L)
+            dz = min_image(Z - cz, L)
+            v -= d * np.exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * w * w))
     return v
 
 
