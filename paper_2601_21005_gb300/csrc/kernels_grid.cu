@@ -26,9 +26,10 @@ template <int N> struct Cfg {
     static constexpr int PLANE_NT2 = 2 * PLANE_NT;
 };
 
-// CTAs per SM the fused plane step is compiled for, by thread count: registers 65536 / (NT MINB)
+// CTAs per SM the fused plane step is compiled for, by thread count: registers 65536 / (NT MINB).
+// The 512-thread 64^2 variant runs at 40 registers, 3 blocks (48 warps) per SM.
 template <int N, int NT> struct PlaneMinB {
-    static constexpr int v = 1024 / NT;
+    static constexpr int v = (N == 64 && NT == 512) ? 3 : 1024 / NT;
     static constexpr int value = N == 128 ? 1 : (v > 6 ? 6 : (v < 1 ? 1 : v));
 };
 
