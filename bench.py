@@ -401,7 +401,7 @@ def run_ours(args, cfg):
                             precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world,
                             cuda_graphs=bool(args.graphs),
                             launch_tuning=dict(zip(('plane_operand_prefetch', 'plane_lookahead', 'pencil_lookahead',
-                                                    'plane_threads_variant'),
+                                                    'plane_variant'),
                                                    pl.tuning)) if pl.tuning else 'defaults',
                             roofline_timing='per-kernel CUDA events over the timed region' if not args.graphs else
                             'per-kernel CUDA events over one extra step (graph replay is timed unprofiled)'),

@@ -94,18 +94,21 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
  *   SGW_TUNE_PLANE_LOOKAHEAD  : each xy-plane pass block also prefetches into L2 the input plane of
  *                               the block this many blocks later in launch order (0 = off, default)
  *   SGW_TUNE_PENCIL_LOOKAHEAD : the same for the z-pencil pass, in pencil blocks (0 = off, default)
- *   SGW_TUNE_PLANE_THREADS    : threads per block of the xy-plane pass of a Chebyshev term: 0 = the
- *                               default shape (n^2/16 for n = 64), 1 = twice as many, one butterfly
- *                               per thread per FFT stage (default 0)
+ *   SGW_TUNE_PLANE_VARIANT    : form of the xy-plane pass: 0 = one block of n^2/16 threads per plane
+ *                               (default), 1 = twice as many threads (one butterfly per thread per
+ *                               FFT stage), 2 = persistent blocks that walk their planes and copy the
+ *                               next plane's input into a second shared-memory buffer (cp.async)
+ *                               while the current one is transformed (n <= 64; at n = 128 it runs
+ *                               as 0)
  * sgw_set_tuning returns SGW_EINVAL for an unknown key or a negative value (a value above 1 for
- * SGW_TUNE_PLANE_OPERANDS and SGW_TUNE_PLANE_THREADS) and drops the context's cached graphs; sgw_get_tuning writes the
- * current value to *value_host.
+ * SGW_TUNE_PLANE_OPERANDS, above 2 for SGW_TUNE_PLANE_VARIANT) and drops the context's cached
+ * graphs; sgw_get_tuning writes the current value to *value_host.
  */
 enum {
     SGW_TUNE_PLANE_OPERANDS = 0,
     SGW_TUNE_PLANE_LOOKAHEAD = 1,
     SGW_TUNE_PENCIL_LOOKAHEAD = 2,
-    SGW_TUNE_PLANE_THREADS = 3,
+    SGW_TUNE_PLANE_VARIANT = 3,
     SGW_TUNE_KEYS = 4
 };
 sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value);
@@ -113,8 +116,8 @@ sgw_status sgw_get_tuning(sgw_ctx* ctx, int key, int* value_host);
 
 /*
  * Autotuner: time `reps` degree-8 Chebyshev sums (the propagator's two-pass term, KB included when
- * a KB part is set) on a scratch batch of `batch` vectors for each candidate value (plane threads
- * 0/1, then operand prefetch 0/1, then the lookaheads 0 and 1/2, 1, 3/2, 2 waves of resident
+ * a KB part is set) on a scratch batch of `batch` vectors for each candidate value (plane-pass
+ * variant 0/1/2, then operand prefetch 0/1, then the lookaheads 0 and 1/2, 1, 3/2, 2 waves of resident
  * blocks from the occupancy of this GPU), keep the fastest per key, each key timed with the
  * choices already made for the keys before it, and write the chosen values to chosen_host
  * [SGW_TUNE_KEYS] (may be NULL).  Needs sgw_set_potential and a spectral interval (SGW_ESTATE

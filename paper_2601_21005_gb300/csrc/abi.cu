@@ -383,7 +383,7 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
             double bytes = per * (double)ctx->ng * batch + 4.0 * (double)ctx->ng * vrows * (dvpot ? 2 : 1);
             if (a.kbc) bytes += 4.0 * (double)ctx->ng + 20.0 * (double)ctx->kb.n_sup;
             Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
-            sgw::launch_plane_step(n, a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_PLANE_THREADS]);
+            sgw::launch_plane_step(n, a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_PLANE_VARIANT]);
             CKL();
         }
     }
@@ -569,7 +569,7 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable) {
 sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value) {
     if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
     if (key < 0 || key >= SGW_TUNE_KEYS) return fail(ctx, SGW_EINVAL, "unknown tuning key");
-    if (value < 0 || ((key == SGW_TUNE_PLANE_OPERANDS || key == SGW_TUNE_PLANE_THREADS) && value > 1))
+    if (value < 0 || (key == SGW_TUNE_PLANE_OPERANDS && value > 1) || (key == SGW_TUNE_PLANE_VARIANT && value > 2))
         return fail(ctx, SGW_EINVAL, "tuning value out of range");
     clear_graphs(ctx);
     ctx->tune[key] = value;
@@ -625,14 +625,15 @@ sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
         }
         return SGW_OK;
     };
-    const int order[SGW_TUNE_KEYS] = {SGW_TUNE_PLANE_THREADS, SGW_TUNE_PLANE_OPERANDS, SGW_TUNE_PLANE_LOOKAHEAD,
+    const int order[SGW_TUNE_KEYS] = {SGW_TUNE_PLANE_VARIANT, SGW_TUNE_PLANE_OPERANDS, SGW_TUNE_PLANE_LOOKAHEAD,
                                       SGW_TUNE_PENCIL_LOOKAHEAD};
     for (int ki = 0; ki < SGW_TUNE_KEYS && !s; ++ki) {
         const int key = order[ki];
         std::vector<int> cand = {0, 1};
+        if (key == SGW_TUNE_PLANE_VARIANT && sgw::plane_pipe_supported(ctx->n)) cand.push_back(2);
         if (key == SGW_TUNE_PLANE_LOOKAHEAD || key == SGW_TUNE_PENCIL_LOOKAHEAD) {
             const int per_sm = key == SGW_TUNE_PLANE_LOOKAHEAD
-                                   ? sgw::plane_step_blocks_per_sm(ctx->n, ctx->tune[SGW_TUNE_PLANE_THREADS], ctx->kb.max_plane_slots)
+                                   ? sgw::plane_step_blocks_per_sm(ctx->n, ctx->tune[SGW_TUNE_PLANE_VARIANT], ctx->kb.max_plane_slots)
                                    : sgw::pencil_blocks_per_sm(ctx->n);
             const int R = per_sm * nsm;
             cand = {0, R / 2, R, (3 * R) / 2, 2 * R};
@@ -726,9 +727,9 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
         const size_t smem = sgw::plane_step_smem(n, max_slots);
         int optin = 0;
         CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-        if (smem > (size_t)optin)
+        if (smem > (size_t)optin || (sgw::plane_pipe_supported(n) && sgw::plane_pipe_smem(n, max_slots) > (size_t)optin))
             return fail(ctx, SGW_EINVAL, "the projector slots of one plane do not fit in shared memory");
-        CK(sgw::plane_step_reserve_smem(n, smem));
+        CK(sgw::plane_step_reserve_smem(n, max_slots));
         std::vector<int> slot_atom(std::max(total_slots, 1));
         std::vector<std::vector<int>> atom_slots(n_atoms);
         for (int z = 0; z < n; ++z)
@@ -880,7 +881,7 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     }
     {
         Launch L(ctx, SGW_PROF_PLANE_STEP);
-        sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream, ctx->tune[SGW_TUNE_PLANE_THREADS]);
+        sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream, ctx->tune[SGW_TUNE_PLANE_VARIANT]);
         CKL();
     }
     return SGW_OK;

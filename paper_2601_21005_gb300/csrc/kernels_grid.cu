@@ -316,48 +316,72 @@ k_energy_reduce(const double* __restrict__ part, int per, int nblk, double dvn, 
 }
 
 // ------------------------------------------------------------------ fused Chebyshev step
-template <int N, int NT>
-__global__ void __launch_bounds__(NT, (PlaneMinB<N, NT>::value))
-k_plane_step(StepArgs a, const float2* __restrict__ tw) {
-    extern __shared__ float2 sm[];
+// Sum 8 per-lane values over a warp by halving exchanges at lane distances 16, 8, 4 (each lane keeps
+// the half selected by its lane bit and adds its partner's copy of that half), then a plain
+// reduction over distances 2 and 1; returns the total of value 4 bit4 + 2 bit3 + bit2 of the lane.
+__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane) {
+    float a4[4], a2[2];
+    const bool h4 = (lane >> 4) & 1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float keep = h4 ? v[4 + i] : v[i], give = h4 ? v[i] : v[4 + i];
+        a4[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+    const bool h3 = (lane >> 3) & 1;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = h3 ? a4[2 + i] : a4[i], give = h3 ? a4[i] : a4[2 + i];
+        a2[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+    const bool h2 = (lane >> 2) & 1;
+    const float keep = h2 ? a2[1] : a2[0], give = h2 ? a2[0] : a2[1];
+    float t = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    return t;
+}
+
+// L2 prefetch of the pointwise operands of plane z of vector b (one thread)
+template <int N>
+__device__ __forceinline__ void prefetch_operands(const StepArgs& a, int z, int b) {
+    constexpr size_t NG = (size_t)N * N * N;
+    constexpr unsigned PB = N * N * sizeof(float2), VB = N * N * sizeof(float);
+    const size_t plane = ((size_t)b * N + z) * N * N;
+    const VecInfo inf = a.info[b];
+    l2_prefetch(a.b1 + plane, PB);
+    if (a.psi != nullptr) l2_prefetch(a.psi + plane, PB);
+    if (a.b2 != nullptr) l2_prefetch(a.b2 + plane, PB);
+    l2_prefetch(a.vpot + (size_t)inf.vrow * NG + (size_t)z * N * N, VB);
+    if (a.dvpot != nullptr && inf.dvrow >= 0) {
+        l2_prefetch(a.dvpot + (size_t)inf.dvrow * NG + (size_t)z * N * N, VB);
+        l2_prefetch(a.b1 + ((size_t)inf.partner * N + z) * N * N, PB);
+    }
+}
+
+// The fused Chebyshev step on plane z of vector b (see k_plane_step).  IN_SMEM: the plane's input
+// W is already in sm (pitch N + 1), else the first inverse stage reads it from global memory.
+template <int N, int NT, bool IN_SMEM>
+__device__ __forceinline__ void plane_step_body(const StepArgs& a, float2* sm, float2* kcs, TwShared tws, int z,
+                                                int b) {
     constexpr int P = N + 1;
     constexpr size_t NG = (size_t)N * N * N;
-    const int z = blockIdx.x, b = blockIdx.y;
     const size_t plane = ((size_t)b * N + z) * N * N;
     const VecInfo inf = a.info[b];
     const float* V = a.vpot + (size_t)inf.vrow * NG + (size_t)z * N * N;
     const float* dV = (a.dvpot != nullptr && inf.dvrow >= 0) ? a.dvpot + (size_t)inf.dvrow * NG + (size_t)z * N * N
                                                                  : nullptr;
     const float2* bp = (dV != nullptr) ? a.b1 + ((size_t)inf.partner * N + z) * N * N : nullptr;
-    if (threadIdx.x == 0 && a.pf_operands) {
-        // the pointwise operands stream into L2 while the inverse transform runs
-        constexpr unsigned PB = N * N * sizeof(float2), VB = N * N * sizeof(float);
-        l2_prefetch(a.b1 + plane, PB);
-        if (a.psi != nullptr) l2_prefetch(a.psi + plane, PB);
-        if (a.b2 != nullptr) l2_prefetch(a.b2 + plane, PB);
-        l2_prefetch(V, VB);
-        if (dV != nullptr) {
-            l2_prefetch(dV, VB);
-            l2_prefetch(bp, PB);
-        }
-    }
-    if (threadIdx.x == 0 && a.pf_ahead > 0) {
-        const long nxt = (long)b * N + z + a.pf_ahead;         // linear id of a later block
-        if (nxt < (long)gridDim.y * N) l2_prefetch(a.W + (size_t)nxt * N * N, N * N * sizeof(float2));
-    }
-    // twiddles and the E-weighted projections of b_{k+1} for the atoms of this plane's slots
-    // (kcs[slot][4]) next to the plane in shared memory
-    float2* stw = sm + N * P;
-    float2* kcs = stw + N;
-    for (int i = threadIdx.x; i < N; i += NT) stw[i] = __ldg(tw + i);
-    const TwShared tws{stw};
     const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
     const int s0 = kc != nullptr ? __ldg(a.plane_off + z) : 0;
     if (kc != nullptr) {
         const int ns = __ldg(a.plane_off + z + 1) - s0;
         for (int i = threadIdx.x; i < 4 * ns; i += NT) kcs[i] = kc[__ldg(a.slot_atom + s0 + i / 4) * 4 + (i & 3)];
     }
-    inv_plane_from_global<N, NT>(sm, a.W + plane, tws);
+    if constexpr (IN_SMEM) {
+        fft2_plane<N, NT, +1>(sm, tws);                // the plane is already in shared memory
+    } else {
+        inv_plane_from_global<N, NT>(sm, a.W + plane, tws);
+    }
     if (kc != nullptr) {
         // KB apply, colour by colour: within a colour every point occurs once, so the adds need no
         // atomics and their order at a point (colour order) is fixed
@@ -365,6 +389,7 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
         for (int c = 0; c < a.max_colors; ++c) {
             const int e0 = __ldg(col + c), e1 = __ldg(col + c + 1);
             if (e0 == e1) break;                  // a plane's colours are used from 0 upwards
+#pragma unroll 4
             for (int e = e0 + threadIdx.x; e < e1; e += NT) {
                 const unsigned os = __ldg(a.kbe_os + e);
                 const float4 be = __ldg(a.kbe_beta + e);
@@ -426,6 +451,7 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
         for (int k = sb + warp; k < s1; k += NT / 32) {
             float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const int e1 = __ldg(a.kbe_slot_end + k);
+#pragma unroll 4
             for (int e = __ldg(a.kbe_slot_beg + k) + lane; e < e1; e += 32) {
                 const int o = (int)(__ldg(a.kbe_os + e) & 0xffffu);
                 const float2 v = sm[(o / N) * P + (o % N)];
@@ -435,13 +461,87 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
                 acc[4] += be.z * v.x; acc[5] += be.z * v.y;
                 acc[6] += be.w * v.x; acc[7] += be.w * v.y;
             }
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-                for (int off = 16; off > 0; off >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off);
-            if (lane < 8) reinterpret_cast<float*>(a.kbp + ((size_t)b * a.total_slots + k) * 4)[lane] = acc[lane];
+            // butterfly reduce-scatter of the 8 sums over the warp (9 shuffles, fixed order): after
+            // it, lane l holds the total of accumulator 4 bit4(l) + 2 bit3(l) + bit2(l)
+            const float r = warp_reduce_scatter8(acc, lane);
+            if ((lane & 3) == 0)
+                reinterpret_cast<float*>(a.kbp + ((size_t)b * a.total_slots + k) * 4)[lane >> 2] = r;
         }
     }
     fwd_plane_to_global<N, NT>(sm, a.Wout + plane, tws);
+}
+
+
+
+template <int N, int NT>
+__global__ void __launch_bounds__(NT, (PlaneMinB<N, NT>::value))
+k_plane_step(StepArgs a, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int P = N + 1;
+    const int z = blockIdx.x, b = blockIdx.y;
+    // the pointwise operands stream into L2 while the inverse transform runs
+    if (threadIdx.x == 0 && a.pf_operands) prefetch_operands<N>(a, z, b);
+    if (threadIdx.x == 0 && a.pf_ahead > 0) {
+        const long nxt = (long)b * N + z + a.pf_ahead;         // linear id of a later block
+        if (nxt < (long)gridDim.y * N) l2_prefetch(a.W + (size_t)nxt * N * N, N * N * sizeof(float2));
+    }
+    // twiddles and the E-weighted projections of b_{k+1} for the atoms of this plane's slots
+    // (kcs[slot][4]) next to the plane in shared memory
+    float2* stw = sm + N * P;
+    float2* kcs = stw + N;
+    for (int i = threadIdx.x; i < N; i += NT) stw[i] = __ldg(tw + i);
+    plane_step_body<N, NT, false>(a, sm, kcs, TwShared{stw}, z, b);
+}
+
+// cp.async of 8 bytes (global -> shared, through L1) and its group controls
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int K> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(K) : "memory");
+}
+
+// plane (N x N complex, row-major in global memory) -> shared memory with pitch N + 1
+template <int N, int NT>
+__device__ __forceinline__ void copy_plane_async(float2* dst, const float2* __restrict__ src) {
+    constexpr int P = N + 1;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < N * N; q += NT) cp_async8(dst + (q / N) * P + (q % N), src + q);
+}
+
+// Persistent form of the fused step: block i takes the planes t = i, i + gridDim.x, ... (t = b N + z,
+// t < total) and double-buffers their W input in shared memory with cp.async, so the next plane's
+// input is in flight while the current one is transformed.  Same arithmetic as k_plane_step.
+template <int N, int NT>
+__global__ void __launch_bounds__(NT, 3)
+k_plane_step_pipe(StepArgs a, const float2* __restrict__ tw, int total) {
+    extern __shared__ float2 sm[];
+    constexpr int P = N + 1;
+    float2* stw = sm + 2 * N * P;
+    float2* kcs = stw + N;
+    for (int i = threadIdx.x; i < N; i += NT) stw[i] = __ldg(tw + i);
+    int t = blockIdx.x;
+    if (t < total) {
+        copy_plane_async<N, NT>(sm, a.W + (size_t)t * N * N);
+        if (threadIdx.x == 0 && a.pf_operands) prefetch_operands<N>(a, t % N, t / N);
+    }
+    cp_async_commit();
+    for (int it = 0; t < total; ++it, t += gridDim.x) {
+        float2* cur = sm + (size_t)(it & 1) * N * P;
+        const int tn = t + gridDim.x;
+        if (tn < total) {
+            copy_plane_async<N, NT>(sm + (size_t)((it + 1) & 1) * N * P, a.W + (size_t)tn * N * N);
+            if (threadIdx.x == 0 && a.pf_operands) prefetch_operands<N>(a, tn % N, tn / N);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();                 // this plane's group has landed (the newest may be in flight)
+        __syncthreads();
+        plane_step_body<N, NT, true>(a, cur, kcs, TwShared{stw}, t % N, t / N);
+        __syncthreads();                    // cur is refilled two iterations later
+    }
+    cp_async_wait<0>();
 }
 
 // ------------------------------------------------------------------ inverse plane pass
@@ -586,11 +686,29 @@ void launch_kb_reduce(const KBDev& kb, const float2* kbp, int batch, float dV, f
 // ------------------------------------------------------------------ launchers
 bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
 
+// SMs of the current device (cached per device)
+static int sm_count() {
+    static int cache[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 1;
+    if (cache[dev] == 0) cudaDeviceGetAttribute(&cache[dev], cudaDevAttrMultiProcessorCount, dev);
+    return cache[dev] > 0 ? cache[dev] : 1;
+}
+
 // Dynamic shared memory of the fused plane step: the plane, the twiddle table and 4
 // projections per KB slot
 size_t plane_step_smem(int n, int max_plane_slots) {
     return sizeof(float2) * ((size_t)n * (n + 2) + 4 * (size_t)max_plane_slots);
 }
+
+// ... and of its persistent double-buffered form (two planes)
+size_t plane_pipe_smem(int n, int max_plane_slots) {
+    return sizeof(float2) * (2 * (size_t)n * (n + 1) + n + 4 * (size_t)max_plane_slots);
+}
+
+// the persistent form exists up to 64^2 planes (two 128^2 planes do not fit in shared memory)
+bool plane_pipe_supported(int n) { return n <= 64; }
 
 template <int N> static cudaError_t set_attrs() {
     cudaError_t e = cudaSuccess;
@@ -608,6 +726,14 @@ template <int N> static cudaError_t set_attrs() {
     if ((e = cudaFuncSetAttribute(k_pencil<N, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_pencil<N, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    if constexpr (N <= 64) {
+        if ((e = cudaFuncSetAttribute(k_plane_step_pipe<N, Cfg<N>::PLANE_NT>,
+                                      cudaFuncAttributePreferredSharedMemoryCarveout, mx)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_plane_step_pipe<N, Cfg<N>::PLANE_NT>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_pipe_smem(N, 0))))
+            return e;
+    }
     const int pss = (int)plane_step_smem(N, 0);
     if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, pss)))
         return e;
@@ -638,14 +764,21 @@ cudaError_t grid_init_attributes(int n) {
     }
 
 // Resident CTAs per SM of the two passes of a Chebyshev term (for the launch-order lookahead)
-cudaError_t plane_step_reserve_smem(int n, size_t bytes) {
+cudaError_t plane_step_reserve_smem(int n, int max_plane_slots) {
     cudaError_t e = cudaSuccess;
+    const int bytes = (int)plane_step_smem(n, max_plane_slots);
     SGW_DISPATCH_N(n, {
         e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)bytes);
+                                 bytes);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)bytes);
+                                     bytes);
+        if constexpr (N <= 64) {
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_plane_step_pipe<N, Cfg<N>::PLANE_NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)plane_pipe_smem(N, max_plane_slots));
+        }
     });
     return e;
 }
@@ -653,11 +786,15 @@ cudaError_t plane_step_reserve_smem(int n, size_t bytes) {
 int plane_step_blocks_per_sm(int n, int variant, int max_plane_slots) {
     int r = 0;
     const size_t sm = plane_step_smem(n, max_plane_slots);
+    if (variant == 2 && !plane_pipe_supported(n)) variant = 0;
     SGW_DISPATCH_N(n, {
         if (variant == 0)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_plane_step<N, Cfg<N>::PLANE_NT>, Cfg<N>::PLANE_NT, sm);
-        else
+        else if (variant == 1)
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_plane_step<N, Cfg<N>::PLANE_NT2>, Cfg<N>::PLANE_NT2, sm);
+        else if constexpr (N <= 64)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_plane_step_pipe<N, Cfg<N>::PLANE_NT>, Cfg<N>::PLANE_NT,
+                                                          plane_pipe_smem(N, max_plane_slots));
     });
     return r;
 }
@@ -697,12 +834,21 @@ void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, fl
 }
 
 void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
-    const size_t sm = plane_step_smem(n, a.kbc != nullptr ? a.max_plane_slots : 0);
+    const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
+    const size_t sm = plane_step_smem(n, slots);
+    if (variant == 2 && !plane_pipe_supported(n)) variant = 0;
     SGW_DISPATCH_N(n, {
-        if (variant == 0)
+        if (variant == 0) {
             k_plane_step<N, Cfg<N>::PLANE_NT><<<dim3(N, batch), Cfg<N>::PLANE_NT, sm, st>>>(a, tw);
-        else
+        } else if (variant == 1) {
             k_plane_step<N, Cfg<N>::PLANE_NT2><<<dim3(N, batch), Cfg<N>::PLANE_NT2, sm, st>>>(a, tw);
+        } else if constexpr (N <= 64) {
+            // one wave of resident blocks, each walking its planes
+            const int total = N * batch;
+            const int grid = std::min(total, std::max(1, plane_step_blocks_per_sm(n, 2, slots)) * sm_count());
+            k_plane_step_pipe<N, Cfg<N>::PLANE_NT><<<grid, Cfg<N>::PLANE_NT, plane_pipe_smem(N, slots), st>>>(a, tw,
+                                                                                                            total);
+        }
     });
 }
 

@@ -91,7 +91,9 @@ bool grid_supported(int n);
 cudaError_t grid_init_attributes(int n);
 int plane_step_blocks_per_sm(int n, int variant, int max_plane_slots);
 size_t plane_step_smem(int n, int max_plane_slots);
-cudaError_t plane_step_reserve_smem(int n, size_t bytes);
+size_t plane_pipe_smem(int n, int max_plane_slots);
+bool plane_pipe_supported(int n);
+cudaError_t plane_step_reserve_smem(int n, int max_plane_slots);
 int pencil_blocks_per_sm(int n);
 void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st);
 // kind: 0 kinetic (T(k)/N^3, capped at ecut if ecut > 0), 1 Coulomb (4 pi/k^2 / N^3, k=0 -> 0)
