@@ -149,7 +149,7 @@ def units_per_step(cfg):
 # DRAM bytes (read + write, ncu) over algorithmic bytes of one 64-vector k_plane_step launch of the
 # current kernel (profiles/plane_step_pencil_64x64.md); traffic per launch = this ratio x the
 # launch's algorithmic bytes.  Must be re-measured whenever the plane kernel changes.
-PLANE_STEP_DRAM_PER_ALG = 831.6 / 806.4
+PLANE_STEP_DRAM_PER_ALG = 839.2 / 806.4
 
 
 def roofline(prof, peaks):
