@@ -229,6 +229,20 @@ sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, do
                          int cheb_deg, const int8_t* dir_host);
 
 /*
+ * Plain propagation by the split-operator scheme (the paper's own time stepper, Sec. 3): each of
+ * the n_steps steps applies, right to left,
+ *   S(dt) = K_desc(dt/2) e^{-i V_loc dt/2} e^{-i T dt} e^{-i V_loc dt/2} K_asc(dt/2),
+ * with e^{-i T dt} exact in k space (two xy-plane passes and one z-pencil pass) and the KB part
+ * split atom by atom, e^{-i tau V_a} = 1 + Q_a (e^{-i tau M_a} - 1) Q_a^T (Q_a R_a = sqrt(dV) beta_a,
+ * M_a = R_a E_a R_a^T), atoms grouped into colours of disjoint supports (greedy in atom order),
+ * K_asc applying colours 0, 1, .. and K_desc the reverse.  Second order in dt, unitary to
+ * rounding, time reversible.  psi_dev [batch][N_g] c64 in place; dir_host as in sgw_propagate.
+ * SGW_ESTATE without a potential; graph mode as in sgw_propagate.
+ */
+sgw_status sgw_propagate_split(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, double dt,
+                               const int8_t* dir_host);
+
+/*
  * Linear-response TDH (Sec. 2.1, first phase) for n_samples Monte-Carlo samples.
  *  eta_dev: [n_samples][n_eta] c64 filtered occupied stochastic orbitals (read only).
  *  source_dev: [n_samples][N_g] float, the source zeta-bar * phi of each sample.
@@ -447,7 +461,8 @@ enum {
     SGW_PROF_SIGMA = 5,        /* Sigma(t) reduction                                       */
     SGW_PROF_TIME_ORDER = 6,   /* time ordering                                            */
     SGW_PROF_OTHER = 7,        /* everything else                                          */
-    SGW_PROF_KINDS = 8
+    SGW_PROF_SPLIT_INV = 8,    /* inverse plane pass of a split-operator step              */
+    SGW_PROF_KINDS = 9
 };
 
 /* enable != 0: from now on record CUDA events on the context's stream around every kernel

@@ -62,6 +62,15 @@ struct sgw_ctx {
         int64_t n_launch;
     };
     std::vector<GraphEntry> graphs;
+    // split-operator KB factors: orthonormalised projectors per support point (atom-major, like
+    // kb.sup_idx), atoms grouped by 3D colour, per-atom M_a = R E R^T (host, 4 x 4), and the
+    // complex factors e^{-i tau M_a} - 1 for tau = +dt/2 and -dt/2 of the last dt
+    float4* kbq = nullptr;
+    int* acol_atoms = nullptr;
+    std::vector<int> acol_off;
+    std::vector<double> kb_m;
+    float2* split_F = nullptr;
+    double split_dt = 0.0;
     // launch tuning hints (sgw_set_tuning / sgw_autotune); no result depends on them
     int tune[SGW_TUNE_KEYS] = {1, 0, 0, 0};
     std::string err;
@@ -290,6 +299,15 @@ void free_kb(sgw_ctx* ctx) {
     kb = sgw::KBDev();
     ctx->kbc = nullptr;
     ctx->kbp = nullptr;
+    void* sp[] = {ctx->kbq, ctx->acol_atoms, ctx->split_F};
+    for (void* p : sp)
+        if (p) cudaFree(p);
+    ctx->kbq = nullptr;
+    ctx->acol_atoms = nullptr;
+    ctx->split_F = nullptr;
+    ctx->acol_off.clear();
+    ctx->kb_m.clear();
+    ctx->split_dt = 0.0;
 }
 
 // KB table pointers of a plane-step launch
@@ -566,6 +584,148 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable) {
     return SGW_OK;
 }
 
+// ---------------------------------------------------------------- split-operator KB factors
+// Eigenvalues/vectors of a symmetric n x n matrix (n <= 4) by cyclic Jacobi rotations:
+// a = w diag(lam) w^T.
+static void jacobi_eig(int n, const double* a_in, double* lam, double* w) {
+    double a[16];
+    for (int i = 0; i < n * n; ++i) a[i] = a_in[i];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) w[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                tot += a[i * n + j] * a[i * n + j];
+                if (i != j) off += a[i * n + j] * a[i * n + j];
+            }
+        if (off <= 1e-30 * (tot + 1e-300)) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a[p * n + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                const double theta = 0.5 * (a[q * n + q] - a[p * n + p]) / apq;
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {       // columns p, q of a
+                    const double akp = a[k * n + p], akq = a[k * n + q];
+                    a[k * n + p] = c * akp - sn * akq;
+                    a[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {       // rows p, q
+                    const double apk = a[p * n + k], aqk = a[q * n + k];
+                    a[p * n + k] = c * apk - sn * aqk;
+                    a[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {       // accumulate the rotation
+                    const double wkp = w[k * n + p], wkq = w[k * n + q];
+                    w[k * n + p] = c * wkp - sn * wkq;
+                    w[k * n + q] = sn * wkp + c * wkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i) lam[i] = a[i * n + i];
+}
+
+// Q (CGS2, FP64) and M = R E R^T of each atom, the 3D greedy colours of the atoms, uploaded.
+static sgw_status build_split_tables(sgw_ctx* ctx, int n_atoms, const int* nproj, const int64_t* sup_off,
+                                     const int* sup_idx, const float* beta, const float* e) {
+    const int64_t nsup = sup_off[n_atoms];
+    const double sdv = std::sqrt(ctx->dV);
+    std::vector<float4> q4(std::max<int64_t>(nsup, 1));
+    ctx->kb_m.assign((size_t)n_atoms * 16, 0.0);
+    for (int a = 0; a < n_atoms; ++a) {
+        const int64_t s0 = sup_off[a], ns = sup_off[a + 1] - s0;
+        const int P = nproj[a];
+        std::vector<double> q((size_t)4 * ns, 0.0);
+        double R[16] = {0.0};
+        for (int p = 0; p < P; ++p) {
+            std::vector<double> v(ns);
+            for (int64_t i = 0; i < ns; ++i) v[i] = sdv * beta[4 * (s0 + i) + p];
+            for (int pass = 0; pass < 2; ++pass)
+                for (int k = 0; k < p; ++k) {
+                    double r = 0.0;
+                    for (int64_t i = 0; i < ns; ++i) r += q[(size_t)k * ns + i] * v[i];
+                    for (int64_t i = 0; i < ns; ++i) v[i] -= r * q[(size_t)k * ns + i];
+                    R[k * 4 + p] += r;
+                }
+            double nrm = 0.0;
+            for (int64_t i = 0; i < ns; ++i) nrm += v[i] * v[i];
+            nrm = std::sqrt(nrm);
+            if (!(nrm > 0.0)) return fail(ctx, SGW_EINVAL, "KB projectors of an atom are linearly dependent");
+            R[p * 4 + p] = nrm;
+            for (int64_t i = 0; i < ns; ++i) q[(size_t)p * ns + i] = v[i] / nrm;
+        }
+        for (int64_t i = 0; i < ns; ++i)
+            q4[s0 + i] = make_float4((float)q[i], (float)q[(size_t)ns + i], (float)q[(size_t)2 * ns + i],
+                                     (float)q[(size_t)3 * ns + i]);
+        double* M = &ctx->kb_m[(size_t)a * 16];
+        for (int i = 0; i < P; ++i)
+            for (int j = 0; j < P; ++j) {
+                double m = 0.0;
+                for (int k = 0; k < P; ++k) m += R[i * 4 + k] * (double)e[4 * a + k] * R[j * 4 + k];
+                M[i * 4 + j] = m;
+            }
+    }
+    // greedy colours: the lowest colour not used by an earlier atom sharing a grid point
+    std::vector<uint32_t> mask(ctx->ng, 0u);
+    std::vector<int> col(n_atoms, 0);
+    int nc = 0;
+    for (int a = 0; a < n_atoms; ++a) {
+        uint32_t used = 0;
+        for (int64_t i = sup_off[a]; i < sup_off[a + 1]; ++i) used |= mask[sup_idx[i]];
+        int c = 0;
+        while (c < 32 && (used >> c & 1u)) ++c;
+        if (c == 32) return fail(ctx, SGW_EINVAL, "more than 32 projector supports overlap at a point");
+        for (int64_t i = sup_off[a]; i < sup_off[a + 1]; ++i) mask[sup_idx[i]] |= 1u << c;
+        col[a] = c;
+        nc = std::max(nc, c + 1);
+    }
+    std::vector<int> atoms;
+    ctx->acol_off.assign(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        ctx->acol_off[c] = (int)atoms.size();
+        for (int a = 0; a < n_atoms; ++a)
+            if (col[a] == c) atoms.push_back(a);
+    }
+    ctx->acol_off[nc] = (int)atoms.size();
+    if (cudaMalloc(&ctx->kbq, sizeof(float4) * q4.size()) != cudaSuccess ||
+        cudaMalloc(&ctx->acol_atoms, sizeof(int) * std::max<size_t>(atoms.size(), 1)) != cudaSuccess ||
+        cudaMalloc(&ctx->split_F, sizeof(float2) * 32 * std::max(n_atoms, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SGW_ENOMEM, "split-operator table allocation failed");
+    }
+    CK(cudaMemcpy(ctx->kbq, q4.data(), sizeof(float4) * q4.size(), cudaMemcpyHostToDevice));
+    if (!atoms.empty()) CK(cudaMemcpy(ctx->acol_atoms, atoms.data(), sizeof(int) * atoms.size(), cudaMemcpyHostToDevice));
+    ctx->split_dt = 0.0;
+    return SGW_OK;
+}
+
+// F_a(tau) = e^{-i tau M_a} - 1 for tau = dt/2 (set 0) and -dt/2 (set 1), uploaded when dt changes
+static sgw_status split_factors(sgw_ctx* ctx, double dt) {
+    const int na = ctx->kb.n_atoms;
+    if (na == 0 || dt == ctx->split_dt) return SGW_OK;
+    std::vector<float2> F((size_t)na * 32);
+    for (int a = 0; a < na; ++a) {
+        double lam[4], w[16];
+        jacobi_eig(4, &ctx->kb_m[(size_t)a * 16], lam, w);
+        for (int set = 0; set < 2; ++set) {
+            const double tau = (set == 0 ? 0.5 : -0.5) * dt;
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j) {
+                    std::complex<double> f = 0.0;
+                    for (int k = 0; k < 4; ++k)
+                        f += w[i * 4 + k] * (std::exp(std::complex<double>(0.0, -tau * lam[k])) - 1.0) * w[j * 4 + k];
+                    F[((size_t)a * 2 + set) * 16 + i * 4 + j] = make_float2((float)f.real(), (float)f.imag());
+                }
+        }
+    }
+    CK(cudaMemcpyAsync(ctx->split_F, F.data(), sizeof(float2) * F.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->split_dt = dt;
+    return SGW_OK;
+}
+
 sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value) {
     if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
     if (key < 0 || key >= SGW_TUNE_KEYS) return fail(ctx, SGW_EINVAL, "unknown tuning key");
@@ -827,6 +987,8 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
         CK(cudaMemcpy(kb.atom_pos_off, atom_pos_off.data(), sizeof(int) * (n_atoms + 1), cudaMemcpyHostToDevice));
         if (total_slots > 0)
             CK(cudaMemcpy(kb.atom_pos, atom_pos.data(), sizeof(int) * total_slots, cudaMemcpyHostToDevice));
+        if ((s = build_split_tables(ctx, n_atoms, nproj_host, sup_off_host, sup_idx_host, beta_host, e_host)))
+            return s;
     }
     ctx->have_potential = true;
     return SGW_OK;
@@ -1123,6 +1285,69 @@ sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, do
         for (int j = 0; j < n_steps; ++j) {
             sgw_status r = run_series(ctx, plan, psi, psi, batch, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps);
             if (r) return r;
+        }
+        return SGW_OK;
+    });
+}
+
+sgw_status sgw_propagate_split(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, double dt,
+                               const int8_t* dir_host) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    if (batch < 0 || batch > ctx->max_batch || n_steps < 0 || (!psi_dev && batch > 0))
+        return fail(ctx, SGW_EINVAL, "bad split-propagate arguments");
+    if (batch == 0 || n_steps == 0) return SGW_OK;
+    SGW_ALIGNED(ctx, psi_dev);
+    std::vector<sgw::VecInfo> info(batch, sgw::VecInfo{0, -1, -1, 0});
+    if (dir_host)
+        for (int b = 0; b < batch; ++b) {
+            if (dir_host[b] != 1 && dir_host[b] != -1) return fail(ctx, SGW_EINVAL, "dir must be +1 or -1");
+            info[b].cset = dir_host[b] > 0 ? 0 : 1;
+        }
+    if ((s = upload_info(ctx, info))) return s;
+    if ((s = split_factors(ctx, dt))) return s;
+    float2* psi = (float2*)psi_dev;
+    const int n = ctx->n;
+    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
+    const int nc = (int)ctx->acol_off.size() - 1;
+    const double vb = (double)ctx->ng * batch;
+    const double kb_bytes = (double)ctx->kb.n_sup * batch * 24.0;     // gather + write back + Q per point
+    auto kb_half = [&](bool descending) -> sgw_status {
+        for (int i = 0; i < nc; ++i) {
+            const int c = descending ? nc - 1 - i : i;
+            const int a0 = ctx->acol_off[c], na = ctx->acol_off[c + 1] - a0;
+            Launch L(ctx, SGW_PROF_KB, 1, kb_bytes * na / std::max(ctx->kb.n_atoms, 1));
+            sgw::launch_kb_split(ctx->acol_atoms + a0, na, ctx->kb, ctx->kbq, ctx->split_F, ctx->info, psi, batch,
+                                 (size_t)ctx->ng, ctx->stream);
+            CKL();
+        }
+        return SGW_OK;
+    };
+    std::vector<uint64_t> key = {7, (uint64_t)batch, (uint64_t)n_steps, bits(dt), (uint64_t)psi,
+                                 fnv(info.data(), sizeof(sgw::VecInfo) * info.size())};
+    return graphed(ctx, key, [&]() {
+        for (int j = 0; j < n_steps; ++j) {
+            sgw_status r;
+            if (ctx->kb.n_atoms > 0 && (r = kb_half(false))) return r;
+            {
+                Launch L(ctx, SGW_PROF_PLANE_FWD, 1, 16.0 * vb + 4.0 * ctx->ng);
+                sgw::launch_plane_fwd_phase(n, psi, ctx->vloc, ctx->info, (float)dt, ctx->W, batch, ctx->tw,
+                                            ctx->stream);
+                CKL();
+            }
+            {
+                Launch L(ctx, SGW_PROF_PENCIL, 1, 16.0 * vb);
+                sgw::launch_pencil(n, ctx->W, batch, 2, kscale, (float)ctx->ecut, ctx->tw, ctx->stream,
+                                   ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD], ctx->info, (float)dt);
+                CKL();
+            }
+            {
+                Launch L(ctx, SGW_PROF_SPLIT_INV, 1, 16.0 * vb + 4.0 * ctx->ng);
+                sgw::launch_plane_inv_phase(n, ctx->W, ctx->vloc, ctx->info, (float)dt, psi, batch, ctx->tw,
+                                            ctx->stream);
+                CKL();
+            }
+            if (ctx->kb.n_atoms > 0 && (r = kb_half(true))) return r;
         }
         return SGW_OK;
     });

@@ -201,7 +201,8 @@ __device__ __forceinline__ void pencil_forward(const float2* __restrict__ base, 
 
 template <int N, int KIND>
 __global__ void __launch_bounds__(Cfg<N>::PENCIL_NT)
-k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restrict__ tw, int pf_ahead) {
+k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restrict__ tw, int pf_ahead,
+         const VecInfo* __restrict__ info, float dt) {
     extern __shared__ float2 sm[];
     constexpr int NT = Cfg<N>::PENCIL_NT, TX = Cfg<N>::TX, NXT = N / TX;
     constexpr int R1 = ZPlan<N>::R1, R2 = ZPlan<N>::R2, R3 = ZPlan<N>::R3;
@@ -222,14 +223,36 @@ k_pencil(float2* __restrict__ W, float kscale, float ecut, const float2* __restr
     float2 c[PL][RL];
     pencil_forward<N, NT, PL, RL>(base, sm, c, tw);
     // k-space multiply on X[l][kz = j + q NBL]
+    if constexpr (KIND == 2) {
+        // split-operator kinetic factor e^{-i s T(k) dt} / N^3, s = +1 or -1 per vector
+        const float sdt = (info[blockIdx.y].cset == 0 ? dt : -dt);
+        constexpr float inv = 1.0f / ((float)N * N * N);
 #pragma unroll
-    for (int p = 0; p < PL; ++p) {
-        const int bb = threadIdx.x + p * NT;
-        if ((TX * NBL) % NT == 0 || bb < TX * NBL) {
-            const int l = bb % TX, j = bb / TX;
+        for (int p = 0; p < PL; ++p) {
+            const int bb = threadIdx.x + p * NT;
+            if ((TX * NBL) % NT == 0 || bb < TX * NBL) {
+                const int l = bb % TX, j = bb / TX;
 #pragma unroll
-            for (int q = 0; q < RL; ++q)
-                c[p][q] = cscale(c[p][q], kspace_factor<N, KIND>(xt * TX + l, ky, j + q * NBL, kscale, ecut));
+                for (int q = 0; q < RL; ++q) {
+                    const int mx = sfreq(xt * TX + l, N), my = sfreq(ky, N), mz = sfreq(j + q * NBL, N);
+                    float tk = 0.5f * kscale * (float)(mx * mx + my * my + mz * mz);
+                    if (ecut > 0.f) tk = fminf(tk, ecut);
+                    float sn, cs;
+                    sincosf(tk * sdt, &sn, &cs);
+                    c[p][q] = cmul(c[p][q], make_float2(cs * inv, -sn * inv));
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int p = 0; p < PL; ++p) {
+            const int bb = threadIdx.x + p * NT;
+            if ((TX * NBL) % NT == 0 || bb < TX * NBL) {
+                const int l = bb % TX, j = bb / TX;
+#pragma unroll
+                for (int q = 0; q < RL; ++q)
+                    c[p][q] = cscale(c[p][q], kspace_factor<N, KIND>(xt * TX + l, ky, j + q * NBL, kscale, ecut));
+            }
         }
     }
     // inverse along z with the reversed plan, first stage from registers
@@ -609,6 +632,116 @@ k_density_fwd(const float2* __restrict__ psi, int n_eta, float weight, float* rh
     fwd_plane_to_global<N, NT>(sm, Wp + ((size_t)s * N + z) * N * N, tw);
 }
 
+// ------------------------------------------------------------------ split-operator passes
+// out plane = forward xy transform of e^{-i s V dt/2} psi (s = +1 or -1 per vector)
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
+k_plane_fwd_phase(const float2* __restrict__ psi, const float* __restrict__ vloc, const VecInfo* __restrict__ info,
+                  float dt, float2* __restrict__ W, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    const int z = blockIdx.x, b = blockIdx.y;
+    const size_t plane = ((size_t)b * N + z) * N * N;
+    const float hdt = 0.5f * (info[b].cset == 0 ? dt : -dt);
+    const float* V = vloc + (size_t)z * N * N;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < N * N / 2; q += NT) {
+        const int y = q / (N / 2), x = 2 * (q % (N / 2));
+        const float4 v = ld4(psi + plane + y * N + x);
+        const float2 pv = __ldg(reinterpret_cast<const float2*>(V + y * N + x));
+        float s0, c0, s1, c1;
+        sincosf(pv.x * hdt, &s0, &c0);
+        sincosf(pv.y * hdt, &s1, &c1);
+        sm[y * P + x] = cmul(make_float2(v.x, v.y), make_float2(c0, -s0));
+        sm[y * P + x + 1] = cmul(make_float2(v.z, v.w), make_float2(c1, -s1));
+    }
+    __syncthreads();
+    fwd_plane_to_global<N, NT>(sm, W + plane, tw);
+}
+
+// psi plane = e^{-i s V dt/2} (inverse xy transform of W)
+template <int N>
+__global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
+k_plane_inv_phase(const float2* __restrict__ W, const float* __restrict__ vloc, const VecInfo* __restrict__ info,
+                  float dt, float2* __restrict__ psi, const float2* __restrict__ tw) {
+    extern __shared__ float2 sm[];
+    constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    const int z = blockIdx.x, b = blockIdx.y;
+    const size_t plane = ((size_t)b * N + z) * N * N;
+    const float hdt = 0.5f * (info[b].cset == 0 ? dt : -dt);
+    const float* V = vloc + (size_t)z * N * N;
+    inv_plane_from_global<N, NT>(sm, W + plane, tw);
+#pragma unroll 4
+    for (int q = threadIdx.x; q < N * N / 2; q += NT) {
+        const int y = q / (N / 2), x = 2 * (q % (N / 2));
+        const float2 pv = __ldg(reinterpret_cast<const float2*>(V + y * N + x));
+        float s0, c0, s1, c1;
+        sincosf(pv.x * hdt, &s0, &c0);
+        sincosf(pv.y * hdt, &s1, &c1);
+        st4(psi + plane + y * N + x, cmul(sm[y * P + x], make_float2(c0, -s0)),
+            cmul(sm[y * P + x + 1], make_float2(c1, -s1)));
+    }
+}
+
+// One colour of the split KB factor: block (i, b) applies e^{-i tau V_a} = 1 + Q_a F_a Q_a^T to
+// vector b for atom a = atoms[i]: c = Q_a^T x over the atom's support (fixed-order block sum),
+// d = F c with F the 4 x 4 complex factor of the vector's direction, x += Q_a d.  Atoms of one
+// colour have disjoint supports, so the blocks of a launch touch disjoint points.
+__global__ void __launch_bounds__(256)
+k_kb_split(const int* __restrict__ atoms, const int64_t* __restrict__ atom_off, const int* __restrict__ sup_idx,
+           const float4* __restrict__ q4, const float2* __restrict__ F /*[n_atoms][2][16]*/,
+           const VecInfo* __restrict__ info, float2* __restrict__ x, size_t ng) {
+    __shared__ float red[8][8];
+    __shared__ float2 d[4];
+    const int a = __ldg(atoms + blockIdx.x), b = blockIdx.y;
+    const int64_t s0 = __ldg(atom_off + a), s1 = __ldg(atom_off + a + 1);
+    float2* v = x + (size_t)b * ng;
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const float2 p = v[__ldg(sup_idx + s)];
+        const float4 q = __ldg(q4 + s);
+        acc[0] += q.x * p.x; acc[1] += q.x * p.y;
+        acc[2] += q.y * p.x; acc[3] += q.y * p.y;
+        acc[4] += q.z * p.x; acc[5] += q.z * p.y;
+        acc[6] += q.w * p.x; acc[7] += q.w * p.y;
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+        if (lane == 0) red[w][i] = acc[i];
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        const int p = threadIdx.x;
+        const float2* f = F + ((size_t)a * 2 + (info[b].cset == 0 ? 0 : 1)) * 16 + p * 4;
+        float2 c[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float re = 0.f, im = 0.f;
+            for (int ww = 0; ww < 8; ++ww) {
+                re += red[ww][2 * k];
+                im += red[ww][2 * k + 1];
+            }
+            c[k] = make_float2(re, im);
+        }
+        float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o = cadd(o, cmul(__ldg(f + k), c[k]));
+        d[p] = o;
+    }
+    __syncthreads();
+    const float2 d0 = d[0], d1 = d[1], d2 = d[2], d3 = d[3];
+    for (int64_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+        const int g = __ldg(sup_idx + s);
+        const float4 q = __ldg(q4 + s);
+        float2 p = v[g];
+        p.x += q.x * d0.x + q.y * d1.x + q.z * d2.x + q.w * d3.x;
+        p.y += q.x * d0.y + q.y * d1.y + q.z * d2.y + q.w * d3.y;
+        v[g] = p;
+    }
+}
+
 // ------------------------------------------------------------------ KB projection
 // kbc[b][4a + p] = E_ap * dV * sum_{r in support(a)} beta_ap(r) b1_b(r)
 __global__ void __launch_bounds__(256)
@@ -725,6 +858,7 @@ template <int N> static cudaError_t set_attrs() {
     if ((e = cudaFuncSetAttribute(k_density_fwd<N>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_pencil<N, 0>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_pencil<N, 1>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_pencil<N, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_plane_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     if constexpr (N <= 64) {
         if ((e = cudaFuncSetAttribute(k_plane_step_pipe<N, Cfg<N>::PLANE_NT>,
@@ -740,6 +874,8 @@ template <int N> static cudaError_t set_attrs() {
     if ((e = cudaFuncSetAttribute(k_plane_step<N, Cfg<N>::PLANE_NT2>, cudaFuncAttributeMaxDynamicSharedMemorySize, pss)))
         return e;
     if ((e = cudaFuncSetAttribute(k_plane_inv<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_fwd_phase<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
+    if ((e = cudaFuncSetAttribute(k_plane_inv_phase<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     if ((e = cudaFuncSetAttribute(k_density_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ps))) return e;
     return e;
 }
@@ -811,13 +947,15 @@ void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float
 }
 
 void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st,
-                   int pf_ahead) {
+                   int pf_ahead, const VecInfo* info, float dt) {
     SGW_DISPATCH_N(n, {
         const dim3 grid((N / Cfg<N>::TX) * N, batch);
         if (kind == 0)
-            k_pencil<N, 0><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw, pf_ahead);
+            k_pencil<N, 0><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw, pf_ahead, info, dt);
+        else if (kind == 1)
+            k_pencil<N, 1><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw, pf_ahead, info, dt);
         else
-            k_pencil<N, 1><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw, pf_ahead);
+            k_pencil<N, 2><<<grid, Cfg<N>::PENCIL_NT, Cfg<N>::PENCIL_SMEM, st>>>(W, kscale, ecut, tw, pf_ahead, info, dt);
     });
 }
 
@@ -863,6 +1001,24 @@ void launch_density_fwd(int n, const float2* psi, int n_samples, int n_eta, floa
                         int store_rho0, float2* Wp, const float2* tw, cudaStream_t st) {
     SGW_DISPATCH_N(n, k_density_fwd<N><<<dim3(N, n_samples), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
                               psi, n_eta, weight, rho0, store_rho0, Wp, tw));
+}
+
+void launch_plane_fwd_phase(int n, const float2* psi, const float* vloc, const VecInfo* info, float dt, float2* W,
+                            int batch, const float2* tw, cudaStream_t st) {
+    SGW_DISPATCH_N(n, k_plane_fwd_phase<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
+                              psi, vloc, info, dt, W, tw));
+}
+
+void launch_plane_inv_phase(int n, const float2* W, const float* vloc, const VecInfo* info, float dt, float2* psi,
+                            int batch, const float2* tw, cudaStream_t st) {
+    SGW_DISPATCH_N(n, k_plane_inv_phase<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
+                              W, vloc, info, dt, psi, tw));
+}
+
+void launch_kb_split(const int* atoms, int n_atoms_colour, const KBDev& kb, const float4* q4, const float2* F,
+                     const VecInfo* info, float2* x, int batch, size_t ng, cudaStream_t st) {
+    if (n_atoms_colour == 0 || batch == 0) return;
+    k_kb_split<<<dim3(n_atoms_colour, batch), 256, 0, st>>>(atoms, kb.atom_off, kb.sup_idx, q4, F, info, x, ng);
 }
 
 void launch_kb_project(int n, const KBDev& kb, const float2* b1, int batch, float dV, float2* kbc, cudaStream_t st) {

@@ -14,7 +14,8 @@ from . import build as _build
 
 _lib = None
 
-PROF_KINDS = ['plane_step', 'pencil', 'kb_project', 'plane_fwd', 'tdh_density', 'sigma', 'time_order', 'other']
+PROF_KINDS = ['plane_step', 'pencil', 'kb_project', 'plane_fwd', 'tdh_density', 'sigma', 'time_order', 'other',
+              'split_inv']
 
 SGW_STATUS = {0: 'SGW_OK', 1: 'SGW_EINVAL', 2: 'SGW_ENOMEM', 3: 'SGW_ECUDA', 4: 'SGW_ESTATE',
               5: 'SGW_ETIMEOUT', 6: 'SGW_ENOCONV'}
@@ -48,6 +49,7 @@ _SIGS = {
     'sgw_white_noise': ([_P, _c.c_uint64, _c.c_uint32, _c.c_int, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_prepare_sample': ([_P, _P, _P, _P, _c.c_int, _c.c_int, _P, _P, _P], _c.c_int),
     'sgw_propagate': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _P], _c.c_int),
+    'sgw_propagate_split': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _P], _c.c_int),
     'sgw_tdh_response': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_double, _P], _c.c_int),
     'sgw_time_order': ([_P, _P, _P, _c.c_int, _c.c_int], _c.c_int),
     'sgw_sigma_c': ([_P, _P, _P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_int, _P], _c.c_int),
@@ -366,6 +368,12 @@ class Context:
         d, pd = _host(dirs, np.int8)
         self._ck('sgw_propagate', lib().sgw_propagate(self._p, _dev(psi, torch.complex64), psi.numel() // self.ng,
                                                      n_steps, dt, cheb_deg, pd))
+
+    def propagate_split(self, psi, n_steps, dt, dirs=None):
+        import torch
+        d, pd = _host(dirs, np.int8)
+        self._ck('sgw_propagate_split', lib().sgw_propagate_split(self._p, _dev(psi, torch.complex64),
+                                                                 psi.numel() // self.ng, n_steps, dt, pd))
 
     def tdh_response(self, eta, source, n_samples, n_eta, n_steps, dt, cheb_deg, uR, weight=0.0):
         import torch
