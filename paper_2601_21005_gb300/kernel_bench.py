@@ -27,6 +27,7 @@ def main():
     ap.add_argument('--tune', default=None,
                     help='semicolon-separated settings "operands,plane_lookahead,pencil_lookahead" to time in turn')
     ap.add_argument('--autotune', action='store_true', help='run the library autotuner first and report its choice')
+    ap.add_argument('--split', action='store_true', help='time the split-operator propagator instead of Chebyshev')
     args = ap.parse_args()
     build.build()
     radius = args.radius if args.radius is not None else (10.5 if args.n >= 64 else 4.5)
@@ -47,19 +48,27 @@ def main():
             for k, v in enumerate(st):
                 ctx.set_tuning(k, v)
         tuning = [ctx.get_tuning(k) for k in range(ctx.TUNE_KEYS)]
-        ctx.propagate(psi, 1, 0.05, args.deg)          # warm-up
+        step = (lambda k: ctx.propagate_split(psi, k, 0.05)) if args.split else \
+            (lambda k: ctx.propagate(psi, k, 0.05, args.deg))
+        step(1)                                          # warm-up
         torch.cuda.synchronize()
         ctx.profile(True)
-        ctx.propagate(psi, args.steps, 0.05, args.deg)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(args.steps)
+        e1.record()
         prof = ctx.profile_read()
         ctx.profile(False)
+        wall_ms = e0.elapsed_time(e1)
         out = {}
         for k, v in prof.items():
             if v['launches']:
                 out[k] = dict(launches=v['launches'], avg_us=round(1e3 * v['ms'] / v['launches'], 2),
                               alg_GBps=round(v['alg_bytes'] / (v['ms'] * 1e-3) / 1e9, 1) if v['alg_bytes'] else None)
         print(json.dumps(dict(n=args.n, batch=args.batch, steps=args.steps, deg=args.deg, tuning=tuning,
-                              autotuned=chosen, kernels=out)), flush=True)
+                              propagator='split' if args.split else 'chebyshev', autotuned=chosen,
+                              pts_vec_steps_per_s=args.n ** 3 * args.batch * args.steps / (wall_ms * 1e-3),
+                              kernels=out)), flush=True)
 
 
 if __name__ == '__main__':
