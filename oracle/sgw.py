@@ -25,6 +25,7 @@ import numpy as np
 
 from . import hamiltonian as ham
 from . import chebyshev as cheb
+from . import splitop
 from .philox import rademacher_words
 
 
@@ -68,13 +69,15 @@ def density(eta, n_eta):
     return (2.0 / n_eta) * np.sum(np.abs(eta) ** 2, axis=0)
 
 
-def tdh_response_tangent(prob, eta, source, n_steps, dt, K, weight=None):
+def tdh_response_tangent(prob, eta, source, n_steps, dt, K, weight=None, split=None):
     """u^R(t_j), j = 0..n_steps, by the tangent-linear (lambda -> 0) pair.
 
     eta: filtered occupied stochastic orbitals [N_eta, n, n, n]; source: zeta-bar * phi.
     The perturbed copy is represented by its derivative with respect to the kick
     strength: d eta(0) = -i v_p eta(0) for the kick e^{-i lambda v_p}.  Each step holds
     H(t_j) fixed.  `weight` replaces 2/N_eta in the density (2 for exact orbitals).
+    split: None for the degree-K Chebyshev step, else the splitop.KBSplit of the KB part
+    (or False without KB) for the split-operator step.
     Returns u^R as a real array [n_steps + 1, n, n, n].
     """
     g = prob.grid
@@ -93,8 +96,14 @@ def tdh_response_tangent(prob, eta, source, n_steps, dt, K, weight=None):
         uR[j] = dv
         if j == n_steps:
             break
-        e, de = cheb.propagate_step_tangent(lambda v: prob.h0(v, dvh), e, de, dv,
-                                            prob.emin, prob.emax, dt, K)
+        if split is None:
+            e, de = cheb.propagate_step_tangent(lambda v: prob.h0(v, dvh), e, de, dv,
+                                                prob.emin, prob.emax, dt, K)
+        else:
+            pair = [splitop.split_step_tangent(e[l], de[l], g, prob.vloc + dvh, dv, split or None, dt)
+                    for l in range(n_eta)]
+            e = np.stack([p[0] for p in pair])
+            de = np.stack([p[1] for p in pair])
     return uR
 
 
@@ -152,7 +161,7 @@ def time_order(uR, M=None):
 
 
 # ---------------------------------------------------------------- zeta propagation and Sigma(t)
-def sigma_t(prob, zeta_occ, zeta_unocc, u, n_steps, dt, K):
+def sigma_t(prob, zeta_occ, zeta_unocc, u, n_steps, dt, K, split=None):
     """Sigma(t_j), j = -N_tau..N_tau, of one sample (Eq. 4 and Eq. 5).
 
     zeta(t) = e^{-i H0 t} zeta_unocc for t > 0 and -e^{-i H0 t} zeta_occ for t < 0;
@@ -174,8 +183,12 @@ def sigma_t(prob, zeta_occ, zeta_unocc, u, n_steps, dt, K):
             out[n_steps - j] = sm
         if j == n_steps:
             break
-        zp = cheb.propagate_step(prob.h0, zp, prob.emin, prob.emax, dt, K)
-        zm = cheb.propagate_step(prob.h0, zm, prob.emin, prob.emax, -dt, K)
+        if split is None:
+            zp = cheb.propagate_step(prob.h0, zp, prob.emin, prob.emax, dt, K)
+            zm = cheb.propagate_step(prob.h0, zm, prob.emin, prob.emax, -dt, K)
+        else:
+            zp = splitop.split_step(zp, g, prob.vloc, split or None, dt)
+            zm = splitop.split_step(zm, g, prob.vloc, split or None, -dt)
     return out
 
 

@@ -95,3 +95,28 @@ def split_propagate(psi, grid, vloc, kbs, dt, n_steps):
     for _ in range(n_steps):
         x = split_step(x, grid, vloc, kbs, dt)
     return x
+
+
+def split_step_tangent(psi, dpsi, grid, v, dv, kbs, dt):
+    """One split step of psi under the local potential v and its derivative along v -> v + lam dv:
+
+        a = K_asc psi,             da = K_asc dpsi
+        b = e^{-i v dt/2} a,       db = e^{-i v dt/2} (da - i (dt/2) dv a)
+        c = e^{-i T dt} b,         dc = e^{-i T dt} db
+        d = e^{-i v dt/2} c,       dd = e^{-i v dt/2} (dc - i (dt/2) dv c)
+        psi' = K_desc d,           dpsi' = K_desc dd
+    (v and dv are diagonal and commute, so d/dlam e^{-i (v + lam dv) dt/2} = -i (dt/2) dv e^{-i v dt/2})."""
+    x, dx = psi.astype(np.complex128), dpsi.astype(np.complex128)
+    if kbs is not None:
+        x = kbs.apply(x, 0.5 * dt, descending=False)
+        dx = kbs.apply(dx, 0.5 * dt, descending=False)
+    half = np.exp(-0.5j * dt * v)
+    x, dx = half * x, half * (dx - 0.5j * dt * dv * x)
+    kin = np.exp(-1j * dt * grid.T)
+    x = np.fft.ifftn(kin * np.fft.fftn(x))
+    dx = np.fft.ifftn(kin * np.fft.fftn(dx))
+    x, dx = half * x, half * (dx - 0.5j * dt * dv * x)
+    if kbs is not None:
+        x = kbs.apply(x, 0.5 * dt, descending=True)
+        dx = kbs.apply(dx, 0.5 * dt, descending=True)
+    return x, dx

@@ -92,3 +92,52 @@ def test_accuracy_next_to_the_chebyshev_step():
                             - ref) / np.linalg.norm(ref)
     print('one step dt = 0.05: split-operator error %.2e, Chebyshev-16 error %.2e' % (e_split, e_cheb))
     assert e_cheb < 1e-11 and 1e-7 < e_split < 1e-2
+
+
+def test_tangent_step_is_the_derivative():
+    g, v, atoms = _system()
+    kbs = splitop.KBSplit(atoms, g)
+    rng = np.random.default_rng(6)
+    psi = rng.normal(size=g.shape()) + 1j * rng.normal(size=g.shape())
+    dpsi = rng.normal(size=g.shape()) + 1j * rng.normal(size=g.shape())
+    dv = rng.normal(size=g.shape())
+    _, got = splitop.split_step_tangent(psi, dpsi, g, v, dv, kbs, 0.05)
+    h = 1e-5
+    fd = (splitop.split_step(psi + h * dpsi, g, v + h * dv, kbs, 0.05)
+          - splitop.split_step(psi - h * dpsi, g, v - h * dv, kbs, 0.05)) / (2 * h)
+    assert np.max(np.abs(got - fd)) < 1e-8 * np.max(np.abs(fd))
+    x, _ = splitop.split_step_tangent(psi, dpsi, g, v, dv, kbs, 0.05)
+    assert np.allclose(x, splitop.split_step(psi, g, v, kbs, 0.05), atol=1e-14)
+
+
+def test_split_tdh_and_sigma_converge_to_the_chebyshev_ones():
+    """With the same inputs, the TDH response and Sigma(t) of the split-operator stepper approach
+    those of the (exact-per-step) Chebyshev stepper as dt^2 at a fixed final time."""
+    from oracle import sgw as osgw
+    g, v, atoms = _system()
+    kb = ham.KB(atoms)
+    kbs = splitop.KBSplit(atoms, g)
+    H = ham.dense_h(g, v, kb)
+    lam, w = np.linalg.eigh(H)
+    lo, hi = lam[0] - 1.0, lam[-1] + 1.0
+    phi = w[:, 2].real.reshape(g.shape()) / np.sqrt(g.dV)
+    prob = osgw.Problem(g, v, kb, lo, hi, lam[1], lam[2], phi)
+    rng = np.random.default_rng(7)
+    eta = np.stack([(w[:, :2] @ rng.normal(size=2)).reshape(g.shape()) for _ in range(2)])
+    src = np.sign(rng.normal(size=g.shape())) * phi
+    t = 0.4
+    diffs = []
+    for n in (8, 16):
+        a = osgw.tdh_response_tangent(prob, eta, src, n, t / n, 16)
+        b = osgw.tdh_response_tangent(prob, eta, src, n, t / n, 16, split=kbs)
+        diffs.append(np.linalg.norm(a[-1] - b[-1]) / np.linalg.norm(a[-1]))
+    assert 3.0 < diffs[0] / diffs[1] < 5.0
+    zo = eta[0]
+    zu = src - zo
+    sd = []
+    for n in (8, 16):
+        u = np.stack([np.cos(2.0 * j * t / n) * phi for j in range(n + 1)]).astype(np.complex128)
+        a = osgw.sigma_t(prob, zo, zu, u, n, t / n, 16)
+        b = osgw.sigma_t(prob, zo, zu, u, n, t / n, 16, split=kbs)
+        sd.append(abs(a[-1] - b[-1]) + abs(a[0] - b[0]))        # Sigma(+-t) at the final time
+    assert 3.0 < sd[0] / sd[1] < 5.0
