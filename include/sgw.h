@@ -253,6 +253,10 @@ sgw_status sgw_propagate_split(sgw_ctx* ctx, void* psi_dev, int batch, int n_ste
  *  (weight <= 0 selects 2/n_eta).
  *  uR_dev: [n_samples][n_steps + 1][N_g] float receives u^R(t_j) = v_C * d rho(t_j).
  *  Requires 2 * n_samples * n_eta <= max_batch.
+ *  cheb_deg >= 1: each step is the degree-cheb_deg Chebyshev expansion (needs a spectral
+ *  interval); cheb_deg = 0: the split-operator step of sgw_propagate_split with V = V_loc +
+ *  v_C * (rho(t_j) - rho(0)), its tangent taking the source -i (dt/2) d v psi in each local
+ *  half-step (d v = v_C * d rho(t_j)).
  */
 sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* source_dev,
                             int n_samples, int n_eta, int n_steps, double dt, int cheb_deg,
@@ -277,7 +281,8 @@ sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_
  *  phi_dev: [N_g] float target orbital; u_dev: [n_samples][n_steps+1][N_g] c64.
  *  sigma_dev: [n_samples][2 n_steps + 1] complex128 (index j + n_steps), written.
  *  fp64_accum = 1 accumulates the reductions in FP64, 0 in FP32.
- *  Requires 2 * n_samples <= max_batch.
+ *  Requires 2 * n_samples <= max_batch.  cheb_deg = 0 propagates by the split-operator step of
+ *  sgw_propagate_split instead of the degree-cheb_deg Chebyshev expansion.
  */
 sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev,
                        int n_samples, int n_steps, double dt, int cheb_deg, int fp64_accum,

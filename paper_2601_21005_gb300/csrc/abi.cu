@@ -69,8 +69,8 @@ struct sgw_ctx {
     int* acol_atoms = nullptr;
     std::vector<int> acol_off;
     std::vector<double> kb_m;
-    float2* split_F = nullptr;
-    double split_dt = 0.0;
+    // one device table per dt used so far (graphs keep pointing at the table of their dt)
+    std::vector<std::pair<double, float2*>> split_tabs;
     // launch tuning hints (sgw_set_tuning / sgw_autotune); no result depends on them
     int tune[SGW_TUNE_KEYS] = {1, 0, 0, 0};
     std::string err;
@@ -299,15 +299,15 @@ void free_kb(sgw_ctx* ctx) {
     kb = sgw::KBDev();
     ctx->kbc = nullptr;
     ctx->kbp = nullptr;
-    void* sp[] = {ctx->kbq, ctx->acol_atoms, ctx->split_F};
+    void* sp[] = {ctx->kbq, ctx->acol_atoms};
     for (void* p : sp)
         if (p) cudaFree(p);
+    for (auto& t : ctx->split_tabs) cudaFree(t.second);
+    ctx->split_tabs.clear();
     ctx->kbq = nullptr;
     ctx->acol_atoms = nullptr;
-    ctx->split_F = nullptr;
     ctx->acol_off.clear();
     ctx->kb_m.clear();
-    ctx->split_dt = 0.0;
 }
 
 // KB table pointers of a plane-step launch
@@ -690,21 +690,26 @@ static sgw_status build_split_tables(sgw_ctx* ctx, int n_atoms, const int* nproj
     }
     ctx->acol_off[nc] = (int)atoms.size();
     if (cudaMalloc(&ctx->kbq, sizeof(float4) * q4.size()) != cudaSuccess ||
-        cudaMalloc(&ctx->acol_atoms, sizeof(int) * std::max<size_t>(atoms.size(), 1)) != cudaSuccess ||
-        cudaMalloc(&ctx->split_F, sizeof(float2) * 32 * std::max(n_atoms, 1)) != cudaSuccess) {
+        cudaMalloc(&ctx->acol_atoms, sizeof(int) * std::max<size_t>(atoms.size(), 1)) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, SGW_ENOMEM, "split-operator table allocation failed");
     }
     CK(cudaMemcpy(ctx->kbq, q4.data(), sizeof(float4) * q4.size(), cudaMemcpyHostToDevice));
     if (!atoms.empty()) CK(cudaMemcpy(ctx->acol_atoms, atoms.data(), sizeof(int) * atoms.size(), cudaMemcpyHostToDevice));
-    ctx->split_dt = 0.0;
     return SGW_OK;
 }
 
-// F_a(tau) = e^{-i tau M_a} - 1 for tau = dt/2 (set 0) and -dt/2 (set 1), uploaded when dt changes
-static sgw_status split_factors(sgw_ctx* ctx, double dt) {
+// F_a(tau) = e^{-i tau M_a} - 1 for tau = dt/2 (set 0) and -dt/2 (set 1): the device table of this
+// dt (built and uploaded on its first use) in *out
+static sgw_status split_factors(sgw_ctx* ctx, double dt, const float2** out) {
     const int na = ctx->kb.n_atoms;
-    if (na == 0 || dt == ctx->split_dt) return SGW_OK;
+    *out = nullptr;
+    if (na == 0) return SGW_OK;
+    for (auto& t : ctx->split_tabs)
+        if (t.first == dt) {
+            *out = t.second;
+            return SGW_OK;
+        }
     std::vector<float2> F((size_t)na * 32);
     for (int a = 0; a < na; ++a) {
         double lam[4], w[16];
@@ -720,9 +725,15 @@ static sgw_status split_factors(sgw_ctx* ctx, double dt) {
                 }
         }
     }
-    CK(cudaMemcpyAsync(ctx->split_F, F.data(), sizeof(float2) * F.size(), cudaMemcpyHostToDevice, ctx->stream));
+    float2* dev = nullptr;
+    if (cudaMalloc(&dev, sizeof(float2) * F.size()) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, SGW_ENOMEM, "split-operator factor allocation failed");
+    }
+    ctx->split_tabs.push_back({dt, dev});
+    CK(cudaMemcpyAsync(dev, F.data(), sizeof(float2) * F.size(), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    ctx->split_dt = dt;
+    *out = dev;
     return SGW_OK;
 }
 
@@ -1290,6 +1301,53 @@ sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, do
     });
 }
 
+// One split-operator step of a batch in place (ctx->info: per-vector direction, potential row,
+// tangent row and partner); split_factors(ctx, dt) must have run.
+static sgw_status split_step_batch(sgw_ctx* ctx, float2* psi, int batch, const float* vpot, const float* dvpot,
+                                   double dt, const float2* F) {
+    const int n = ctx->n;
+    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
+    const int nc = (int)ctx->acol_off.size() - 1;
+    const double vb = (double)ctx->ng * batch;
+    const double kb_bytes = (double)ctx->kb.n_sup * batch * 24.0;     // gather + write back + Q per point
+    auto kb_half = [&](bool descending) -> sgw_status {
+        for (int i = 0; i < nc; ++i) {
+            const int c = descending ? nc - 1 - i : i;
+            const int a0 = ctx->acol_off[c], na = ctx->acol_off[c + 1] - a0;
+            Launch L(ctx, SGW_PROF_KB, 1, kb_bytes * na / std::max(ctx->kb.n_atoms, 1));
+            sgw::launch_kb_split(ctx->acol_atoms + a0, na, ctx->kb, ctx->kbq, F, ctx->info, psi, batch,
+                                 (size_t)ctx->ng, ctx->stream);
+            CKL();
+        }
+        return SGW_OK;
+    };
+    sgw_status r;
+    if (ctx->kb.n_atoms > 0 && (r = kb_half(false))) return r;
+    {
+        Launch L(ctx, SGW_PROF_PLANE_FWD, 1, (dvpot ? 24.0 : 16.0) * vb + 8.0 * ctx->ng);
+        sgw::launch_plane_fwd_phase(n, psi, vpot, dvpot, ctx->info, (float)dt, ctx->W, batch, ctx->tw, ctx->stream);
+        CKL();
+    }
+    {
+        Launch L(ctx, SGW_PROF_PENCIL, 1, 16.0 * vb);
+        sgw::launch_pencil(n, ctx->W, batch, 2, kscale, (float)ctx->ecut, ctx->tw, ctx->stream,
+                           ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD], ctx->info, (float)dt);
+        CKL();
+    }
+    {
+        Launch L(ctx, SGW_PROF_SPLIT_INV, 1, 16.0 * vb + 4.0 * ctx->ng);
+        sgw::launch_plane_inv_phase(n, ctx->W, vpot, ctx->info, (float)dt, psi, batch, ctx->tw, ctx->stream);
+        CKL();
+    }
+    if (dvpot != nullptr) {
+        Launch L(ctx, SGW_PROF_OTHER, 1, 14.0 * vb);     // tangent halves: own + partner + dv
+        sgw::launch_split_tangent(psi, dvpot, ctx->info, (float)dt, batch, ctx->ng, ctx->stream);
+        CKL();
+    }
+    if (ctx->kb.n_atoms > 0 && (r = kb_half(true))) return r;
+    return SGW_OK;
+}
+
 sgw_status sgw_propagate_split(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, double dt,
                                const int8_t* dir_host) {
     sgw_status s = check_ctx(ctx, true);
@@ -1305,50 +1363,14 @@ sgw_status sgw_propagate_split(sgw_ctx* ctx, void* psi_dev, int batch, int n_ste
             info[b].cset = dir_host[b] > 0 ? 0 : 1;
         }
     if ((s = upload_info(ctx, info))) return s;
-    if ((s = split_factors(ctx, dt))) return s;
+    const float2* F = nullptr;
+    if ((s = split_factors(ctx, dt, &F))) return s;
     float2* psi = (float2*)psi_dev;
-    const int n = ctx->n;
-    const float kscale = (float)std::pow(2.0 * M_PI / ctx->L, 2);
-    const int nc = (int)ctx->acol_off.size() - 1;
-    const double vb = (double)ctx->ng * batch;
-    const double kb_bytes = (double)ctx->kb.n_sup * batch * 24.0;     // gather + write back + Q per point
-    auto kb_half = [&](bool descending) -> sgw_status {
-        for (int i = 0; i < nc; ++i) {
-            const int c = descending ? nc - 1 - i : i;
-            const int a0 = ctx->acol_off[c], na = ctx->acol_off[c + 1] - a0;
-            Launch L(ctx, SGW_PROF_KB, 1, kb_bytes * na / std::max(ctx->kb.n_atoms, 1));
-            sgw::launch_kb_split(ctx->acol_atoms + a0, na, ctx->kb, ctx->kbq, ctx->split_F, ctx->info, psi, batch,
-                                 (size_t)ctx->ng, ctx->stream);
-            CKL();
-        }
-        return SGW_OK;
-    };
     std::vector<uint64_t> key = {7, (uint64_t)batch, (uint64_t)n_steps, bits(dt), (uint64_t)psi,
                                  fnv(info.data(), sizeof(sgw::VecInfo) * info.size())};
     return graphed(ctx, key, [&]() {
-        for (int j = 0; j < n_steps; ++j) {
-            sgw_status r;
-            if (ctx->kb.n_atoms > 0 && (r = kb_half(false))) return r;
-            {
-                Launch L(ctx, SGW_PROF_PLANE_FWD, 1, 16.0 * vb + 4.0 * ctx->ng);
-                sgw::launch_plane_fwd_phase(n, psi, ctx->vloc, ctx->info, (float)dt, ctx->W, batch, ctx->tw,
-                                            ctx->stream);
-                CKL();
-            }
-            {
-                Launch L(ctx, SGW_PROF_PENCIL, 1, 16.0 * vb);
-                sgw::launch_pencil(n, ctx->W, batch, 2, kscale, (float)ctx->ecut, ctx->tw, ctx->stream,
-                                   ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD], ctx->info, (float)dt);
-                CKL();
-            }
-            {
-                Launch L(ctx, SGW_PROF_SPLIT_INV, 1, 16.0 * vb + 4.0 * ctx->ng);
-                sgw::launch_plane_inv_phase(n, ctx->W, ctx->vloc, ctx->info, (float)dt, psi, batch, ctx->tw,
-                                            ctx->stream);
-                CKL();
-            }
-            if (ctx->kb.n_atoms > 0 && (r = kb_half(true))) return r;
-        }
+        for (int j = 0; j < n_steps; ++j)
+            if (sgw_status r = split_step_batch(ctx, psi, batch, ctx->vloc, nullptr, dt, F)) return r;
         return SGW_OK;
     });
 }
@@ -1357,8 +1379,8 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
                             int n_steps, double dt, int cheb_deg, double weight, float* uR_dev) {
     sgw_status s = check_ctx(ctx, true);
     if (s) return s;
-    if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
-    if (n_samples < 0 || n_eta < 1 || n_steps < 0 || cheb_deg < 1 || 2LL * n_samples * n_eta > ctx->max_batch)
+    if (cheb_deg > 0 && !ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
+    if (n_samples < 0 || n_eta < 1 || n_steps < 0 || cheb_deg < 0 || 2LL * n_samples * n_eta > ctx->max_batch)
         return fail(ctx, SGW_EINVAL, "bad TDH arguments (2 n_samples n_eta must be <= max_batch)");
     if (n_samples == 0) return SGW_OK;
     if (!eta_dev || !source_dev || !uR_dev) return fail(ctx, SGW_EINVAL, "null TDH pointers");
@@ -1389,8 +1411,14 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
     if ((s = upload_info(ctx, info))) return s;
     std::vector<cd> c[2];
     cd ph[2];
-    prop_coeffs(ctx, dt, cheb_deg, c, ph);
-    const std::vector<Step> plan = clenshaw_plan(c, ph, cheb_deg);
+    std::vector<Step> plan;
+    const float2* F = nullptr;
+    if (cheb_deg > 0) {
+        prop_coeffs(ctx, dt, cheb_deg, c, ph);
+        plan = clenshaw_plan(c, ph, cheb_deg);
+    } else if ((s = split_factors(ctx, dt, &F))) {
+        return s;
+    }
     const int64_t uR_stride = (int64_t)(n_steps + 1) * ng;
     std::vector<uint64_t> key = {3, (uint64_t)n_samples, (uint64_t)n_eta, (uint64_t)n_steps, bits(dt),
                                  (uint64_t)cheb_deg, bits(w), (uint64_t)eta_dev, (uint64_t)source_dev, (uint64_t)uR_dev,
@@ -1424,7 +1452,11 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
             }
             CKL();
             if (j == n_steps) break;
-            if (sgw_status s2 = run_series(ctx, plan, psi, psi, B, vtot, dv, ctx->info, j > 0, true, n_samples)) return s2;
+            if (cheb_deg == 0) {
+                if (sgw_status s2 = split_step_batch(ctx, psi, B, vtot, dv, dt, F)) return s2;
+            } else if (sgw_status s2 = run_series(ctx, plan, psi, psi, B, vtot, dv, ctx->info, j > 0, true, n_samples)) {
+                return s2;
+            }
         }
         return SGW_OK;
     });
@@ -1461,8 +1493,8 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
                        double dt, int cheb_deg, int fp64_accum, double* sigma_dev) {
     sgw_status s = check_ctx(ctx, true);
     if (s) return s;
-    if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
-    if (n_samples < 0 || n_steps < 0 || cheb_deg < 1 || 2 * n_samples > ctx->max_batch)
+    if (cheb_deg > 0 && !ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
+    if (n_samples < 0 || n_steps < 0 || cheb_deg < 0 || 2 * n_samples > ctx->max_batch)
         return fail(ctx, SGW_EINVAL, "bad sigma arguments (2 n_samples must be <= max_batch)");
     if (n_samples == 0) return SGW_OK;
     if (!zeta_dev || !phi_dev || !u_dev || !sigma_dev) return fail(ctx, SGW_EINVAL, "null sigma pointers");
@@ -1476,8 +1508,14 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
     double2* partial = (double2*)p;
     std::vector<cd> c[2];
     cd ph[2];
-    prop_coeffs(ctx, dt, cheb_deg, c, ph);
-    const std::vector<Step> plan = clenshaw_plan(c, ph, cheb_deg);
+    std::vector<Step> plan;
+    const float2* F = nullptr;
+    if (cheb_deg > 0) {
+        prop_coeffs(ctx, dt, cheb_deg, c, ph);
+        plan = clenshaw_plan(c, ph, cheb_deg);
+    } else if ((s = split_factors(ctx, dt, &F))) {
+        return s;
+    }
     std::vector<sgw::VecInfo> info(B);
     for (int sm = 0; sm < n_samples; ++sm) {
         info[2 * sm] = sgw::VecInfo{0, -1, -1, 1};      // zeta_occ: backwards, e^{+i H t}
@@ -1498,8 +1536,12 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
             CKL();
         }
         if (j == n_steps) break;
-        if (sgw_status s2 = run_series(ctx, plan, z, z, B, ctx->vloc, nullptr, ctx->info, j > 0, j + 1 < n_steps))
+        if (cheb_deg == 0) {
+            if (sgw_status s2 = split_step_batch(ctx, z, B, ctx->vloc, nullptr, dt, F)) return s2;
+        } else if (sgw_status s2 = run_series(ctx, plan, z, z, B, ctx->vloc, nullptr, ctx->info, j > 0,
+                                               j + 1 < n_steps)) {
             return s2;
+        }
     }
     {
         Launch L(ctx, SGW_PROF_OTHER);

@@ -633,43 +633,63 @@ k_density_fwd(const float2* __restrict__ psi, int n_eta, float weight, float* rh
 }
 
 // ------------------------------------------------------------------ split-operator passes
-// out plane = forward xy transform of e^{-i s V dt/2} psi (s = +1 or -1 per vector)
+// out plane = forward xy transform of e^{-i s V dt/2} x (s = +1 or -1 per vector), V = the vector's
+// row of vpot; for a tangent vector (dvpot given, dvrow >= 0) x = psi - i s (dt/2) dv psi_partner,
+// the derivative of the half-step along V -> V + lam dv (V and dv are diagonal and commute).
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
-k_plane_fwd_phase(const float2* __restrict__ psi, const float* __restrict__ vloc, const VecInfo* __restrict__ info,
-                  float dt, float2* __restrict__ W, const float2* __restrict__ tw) {
+k_plane_fwd_phase(const float2* __restrict__ psi, const float* __restrict__ vpot, const float* __restrict__ dvpot,
+                  const VecInfo* __restrict__ info, float dt, float2* __restrict__ W, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    constexpr size_t NG = (size_t)N * N * N;
     const int z = blockIdx.x, b = blockIdx.y;
     const size_t plane = ((size_t)b * N + z) * N * N;
-    const float hdt = 0.5f * (info[b].cset == 0 ? dt : -dt);
-    const float* V = vloc + (size_t)z * N * N;
+    const VecInfo inf = info[b];
+    const float hdt = 0.5f * (inf.cset == 0 ? dt : -dt);
+    const float* V = vpot + (size_t)inf.vrow * NG + (size_t)z * N * N;
+    const bool tan = dvpot != nullptr && inf.dvrow >= 0;
+    const float* dV = tan ? dvpot + (size_t)inf.dvrow * NG + (size_t)z * N * N : nullptr;
+    const float2* pp = tan ? psi + ((size_t)inf.partner * N + z) * N * N : nullptr;
 #pragma unroll 4
     for (int q = threadIdx.x; q < N * N / 2; q += NT) {
         const int y = q / (N / 2), x = 2 * (q % (N / 2));
-        const float4 v = ld4(psi + plane + y * N + x);
-        const float2 pv = __ldg(reinterpret_cast<const float2*>(V + y * N + x));
+        const int o = y * N + x;
+        const float4 v = ld4(psi + plane + o);
+        float2 a0 = make_float2(v.x, v.y), a1 = make_float2(v.z, v.w);
+        if (tan) {
+            const float4 pa = ld4(pp + o);
+            const float2 d = __ldg(reinterpret_cast<const float2*>(dV + o));
+            // a -= i hdt dv p
+            a0.x += hdt * d.x * pa.y;
+            a0.y -= hdt * d.x * pa.x;
+            a1.x += hdt * d.y * pa.w;
+            a1.y -= hdt * d.y * pa.z;
+        }
+        const float2 pv = __ldg(reinterpret_cast<const float2*>(V + o));
         float s0, c0, s1, c1;
         sincosf(pv.x * hdt, &s0, &c0);
         sincosf(pv.y * hdt, &s1, &c1);
-        sm[y * P + x] = cmul(make_float2(v.x, v.y), make_float2(c0, -s0));
-        sm[y * P + x + 1] = cmul(make_float2(v.z, v.w), make_float2(c1, -s1));
+        sm[y * P + x] = cmul(a0, make_float2(c0, -s0));
+        sm[y * P + x + 1] = cmul(a1, make_float2(c1, -s1));
     }
     __syncthreads();
     fwd_plane_to_global<N, NT>(sm, W + plane, tw);
 }
 
-// psi plane = e^{-i s V dt/2} (inverse xy transform of W)
+// psi plane = e^{-i s V dt/2} (inverse xy transform of W), V = the vector's row of vpot
 template <int N>
 __global__ void __launch_bounds__(Cfg<N>::PLANE_NT, Cfg<N>::PLANE_MINB)
-k_plane_inv_phase(const float2* __restrict__ W, const float* __restrict__ vloc, const VecInfo* __restrict__ info,
+k_plane_inv_phase(const float2* __restrict__ W, const float* __restrict__ vpot, const VecInfo* __restrict__ info,
                   float dt, float2* __restrict__ psi, const float2* __restrict__ tw) {
     extern __shared__ float2 sm[];
     constexpr int NT = Cfg<N>::PLANE_NT, P = N + 1;
+    constexpr size_t NG = (size_t)N * N * N;
     const int z = blockIdx.x, b = blockIdx.y;
     const size_t plane = ((size_t)b * N + z) * N * N;
-    const float hdt = 0.5f * (info[b].cset == 0 ? dt : -dt);
-    const float* V = vloc + (size_t)z * N * N;
+    const VecInfo inf = info[b];
+    const float hdt = 0.5f * (inf.cset == 0 ? dt : -dt);
+    const float* V = vpot + (size_t)inf.vrow * NG + (size_t)z * N * N;
     inv_plane_from_global<N, NT>(sm, W + plane, tw);
 #pragma unroll 4
     for (int q = threadIdx.x; q < N * N / 2; q += NT) {
@@ -680,6 +700,29 @@ k_plane_inv_phase(const float2* __restrict__ W, const float* __restrict__ vloc, 
         sincosf(pv.y * hdt, &s1, &c1);
         st4(psi + plane + y * N + x, cmul(sm[y * P + x], make_float2(c0, -s0)),
             cmul(sm[y * P + x + 1], make_float2(c1, -s1)));
+    }
+}
+
+// Tangent source of the second local half-step: for each tangent vector b (dvrow >= 0),
+// psi_b -= i s (dt/2) dv psi_partner, after k_plane_inv_phase has written both vectors.
+__global__ void __launch_bounds__(256)
+k_split_tangent(float2* __restrict__ psi, const float* __restrict__ dvpot, const VecInfo* __restrict__ info, float dt,
+                int64_t ng) {
+    const VecInfo inf = info[blockIdx.y];
+    if (inf.dvrow < 0) return;
+    const float hdt = 0.5f * (inf.cset == 0 ? dt : -dt);
+    float4* x = reinterpret_cast<float4*>(psi + (size_t)blockIdx.y * ng);
+    const float4* p = reinterpret_cast<const float4*>(psi + (size_t)inf.partner * ng);
+    const float2* d = reinterpret_cast<const float2*>(dvpot + (size_t)inf.dvrow * ng);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ng / 2; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 a = x[i];
+        const float4 pa = p[i];
+        const float2 dv = d[i];
+        a.x += hdt * dv.x * pa.y;
+        a.y -= hdt * dv.x * pa.x;
+        a.z += hdt * dv.y * pa.w;
+        a.w -= hdt * dv.y * pa.z;
+        x[i] = a;
     }
 }
 
@@ -1003,16 +1046,22 @@ void launch_density_fwd(int n, const float2* psi, int n_samples, int n_eta, floa
                               psi, n_eta, weight, rho0, store_rho0, Wp, tw));
 }
 
-void launch_plane_fwd_phase(int n, const float2* psi, const float* vloc, const VecInfo* info, float dt, float2* W,
-                            int batch, const float2* tw, cudaStream_t st) {
+void launch_plane_fwd_phase(int n, const float2* psi, const float* vpot, const float* dvpot, const VecInfo* info,
+                            float dt, float2* W, int batch, const float2* tw, cudaStream_t st) {
     SGW_DISPATCH_N(n, k_plane_fwd_phase<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
-                              psi, vloc, info, dt, W, tw));
+                              psi, vpot, dvpot, info, dt, W, tw));
 }
 
-void launch_plane_inv_phase(int n, const float2* W, const float* vloc, const VecInfo* info, float dt, float2* psi,
+void launch_plane_inv_phase(int n, const float2* W, const float* vpot, const VecInfo* info, float dt, float2* psi,
                             int batch, const float2* tw, cudaStream_t st) {
     SGW_DISPATCH_N(n, k_plane_inv_phase<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
-                              W, vloc, info, dt, psi, tw));
+                              W, vpot, info, dt, psi, tw));
+}
+
+void launch_split_tangent(float2* psi, const float* dvpot, const VecInfo* info, float dt, int batch, int64_t ng,
+                          cudaStream_t st) {
+    const unsigned bx = (unsigned)std::min<int64_t>((ng / 2 + 255) / 256, 256);
+    k_split_tangent<<<dim3(bx, batch), 256, 0, st>>>(psi, dvpot, info, dt, ng);
 }
 
 void launch_kb_split(const int* atoms, int n_atoms_colour, const KBDev& kb, const float4* q4, const float2* F,

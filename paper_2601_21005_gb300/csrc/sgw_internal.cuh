@@ -99,8 +99,10 @@ void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float
 // kind: 0 kinetic (T(k)/N^3, capped at ecut if ecut > 0), 1 Coulomb (4 pi/k^2 / N^3, k=0 -> 0)
 void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw,
                    cudaStream_t st, int pf_ahead = 0, const VecInfo* info = nullptr, float dt = 0.f);
-void launch_plane_fwd_phase(int n, const float2* psi, const float* vloc, const VecInfo* info, float dt, float2* W,
-                            int batch, const float2* tw, cudaStream_t st);
+void launch_plane_fwd_phase(int n, const float2* psi, const float* vpot, const float* dvpot, const VecInfo* info,
+                            float dt, float2* W, int batch, const float2* tw, cudaStream_t st);
+void launch_split_tangent(float2* psi, const float* dvpot, const VecInfo* info, float dt, int batch, int64_t ng,
+                          cudaStream_t st);
 void launch_plane_inv_phase(int n, const float2* W, const float* vloc, const VecInfo* info, float dt, float2* psi,
                             int batch, const float2* tw, cudaStream_t st);
 void launch_kb_split(const int* atoms, int n_atoms_colour, const KBDev& kb, const float4* q4, const float2* F,

@@ -19,7 +19,7 @@ class Pipeline:
     def __init__(self, n, h, vloc, kb_atoms, phi, e_homo, e_lumo, n_eta=8, n_steps=200, dt=0.05,
                  cheb_deg=16, n_cheb=128, samples_per_batch=1, seed=1000, stream_id=1, device=0, ecut=0.0,
                  spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None, graphs=False,
-                 autotune=False, zeta_group=1):
+                 autotune=False, zeta_group=1, propagator='chebyshev'):
         import torch
         self.torch = torch
         # CUDA graphs need a non-default stream: the pipeline then owns one, and its buffers are
@@ -28,7 +28,13 @@ class Pipeline:
         if self.stream is not None:
             stream = self.stream.cuda_stream
         self.n, self.h, self.ng = n, h, n ** 3
-        self.n_eta, self.n_steps, self.dt, self.cheb_deg = n_eta, n_steps, dt, cheb_deg
+        if propagator not in ('chebyshev', 'split'):
+            raise ValueError('propagator must be chebyshev or split')
+        # the time steps of the TDH and zeta phases: degree-cheb_deg Chebyshev, or the split operator
+        # (the library selects it with degree 0); the occupied filter is a Chebyshev series either way
+        self.propagator = propagator
+        self.n_eta, self.n_steps, self.dt = n_eta, n_steps, dt
+        self.cheb_deg = 0 if propagator == 'split' else cheb_deg
         # a run is zeta_group chunks of samples_per_batch samples: white noise, filter, exchange, TDH and
         # time ordering chunk by chunk (2 N_eta samples_per_batch TDH orbitals per launch), then the
         # zeta pairs of all the run's samples in one propagation (2 samples_per_batch zeta_group

@@ -76,3 +76,61 @@ def test_split_graph_replay_is_bit_identical():
             xs.append(x)
     st.synchronize()
     assert torch.equal(xs[0], xs[1])
+
+
+def test_split_tdh_and_sigma_match_the_split_oracle():
+    """The TDH tangent pair and Sigma(t) with the split-operator step (cheb_deg = 0) against the
+    oracle's split-operator forms, on the 32^3 cluster with KB projectors."""
+    from oracle import sgw as osgw
+    build.build()
+    s = gc.small_cluster()
+    g = ham.Grid(s['n'], s['h'])
+    kb = ham.KB(s['kb_atoms'])
+    kbs = splitop.KBSplit(s['kb_atoms'], g)
+    rng = np.random.default_rng(8)
+    n_s, n_eta, N = 2, 3, 12
+    phi = synth.smooth_orbital(g.n, g.h, (8.0, 8.0, 8.0))
+    eta = (0.05 * (rng.normal(size=(n_s, n_eta) + g.shape()) + 1j * rng.normal(size=(n_s, n_eta) + g.shape()))
+           ).astype(np.complex64)
+    src = (np.sign(rng.normal(size=(n_s,) + g.shape())) * phi).astype(np.float32)
+    c = _ctx(s, 2 * n_s * n_eta)
+    uR = torch.empty(n_s, N + 1, g.ng, dtype=torch.float32, device='cuda')
+    c.tdh_response(gc.to_dev(eta.reshape(n_s * n_eta, -1), torch, torch.complex64),
+                   gc.to_dev(src.reshape(n_s, -1), torch, torch.float32), n_s, n_eta, N, 0.05, 0, uR)
+    got = uR.cpu().numpy().reshape((n_s, N + 1) + g.shape())
+    prob = osgw.Problem(g, s['vloc'], kb, -5.0, 70.0, 0, 0, phi)
+    for si in range(n_s):
+        ref = osgw.tdh_response_tangent(prob, eta[si].astype(np.complex128), src[si].astype(np.float64), N, 0.05,
+                                        16, split=kbs)
+        assert gc.rel_err(got[si], ref) < 2e-4
+    zeta = (rng.normal(size=(n_s, 2) + g.shape()) + 1j * rng.normal(size=(n_s, 2) + g.shape())).astype(np.complex64)
+    u = (0.3 * (rng.normal(size=(n_s, N + 1) + g.shape()) + 1j * rng.normal(size=(n_s, N + 1) + g.shape()))
+         ).astype(np.complex64)
+    sig = torch.empty(n_s, 2 * N + 1, dtype=torch.complex128, device='cuda')
+    c.sigma_c(gc.to_dev(zeta.reshape(2 * n_s, -1), torch, torch.complex64),
+              gc.to_dev(phi.ravel().astype(np.float32), torch, torch.float32),
+              gc.to_dev(u.reshape(n_s, N + 1, -1), torch, torch.complex64), n_s, N, 0.05, 0, sig, 1)
+    got = sig.cpu().numpy()
+    for si in range(n_s):
+        ref = osgw.sigma_t(prob, zeta[si, 0].astype(np.complex128), zeta[si, 1].astype(np.complex128),
+                           u[si].astype(np.complex128), N, 0.05, 16, split=kbs)
+        assert gc.rel_err(got[si], ref) < 2e-4
+
+
+def test_split_pipeline_tracks_the_chebyshev_pipeline():
+    """The whole 16^3 sample with split-operator TDH and zeta steps stays within the split scheme's
+    O(dt^2) error of the Chebyshev pipeline on the same samples (200 steps of dt = 0.05)."""
+    from paper_2601_21005_gb300.pipeline import Pipeline
+    build.build()
+    s = synth.wells()
+    g, kb, w, phis = gc.oracle_eigs(s, 8)
+    res = {}
+    for prop in ('chebyshev', 'split'):
+        pl = Pipeline(s['n'], s['h'], s['vloc'], [], phis[3], w[3], w[4], n_eta=8, n_steps=200, dt=0.05,
+                      cheb_deg=16, n_cheb=128, samples_per_batch=2, seed=12, spectrum=(-4.0, 45.0), propagator=prop)
+        sig, x = pl.run(4)
+        res[prop] = (sig.cpu().numpy(), x.cpu().numpy(), pl.qp(sig, x, w[3])['eps_qp'])
+    a, b = res['chebyshev'], res['split']
+    assert np.array_equal(a[1], b[1])                       # the exchange does not propagate
+    assert np.linalg.norm(a[0] - b[0]) < 2e-2 * np.linalg.norm(a[0])
+    assert abs(a[2] - b[2]) * 27.2114 < 0.05
