@@ -435,6 +435,34 @@ def precision_comparison(cfg, sysd, ks, device, seed, pl, base):
                 diff_eV=abs(out['plain_fp32'] - out['mixed_fp64']) * HA_EV, samples=ns)
 
 
+def split_pipeline(cfg, pl, runs=1):
+    """Whole bench steps with the split-operator TDH and zeta steps (the paper's stepper) on the same
+    pipeline, timed with CUDA events; the QP energy of the same samples by both steppers."""
+    import torch
+    ns = pl.run_samples
+    n = runs * ns
+    res = {}
+    for prop, deg in (('split', 0), ('chebyshev', cfg['cheb_deg'])):
+        pl.cheb_deg = deg
+        sig = torch.empty(n, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device=pl.dev)
+        xs = torch.empty(n, dtype=torch.float64, device=pl.dev)
+        pl.run_batch(800000, sig[:ns], xs[:ns])                       # warm-up (graph capture)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for r in range(runs):
+            pl.run_batch(800000 + r * ns, sig[r * ns:(r + 1) * ns], xs[r * ns:(r + 1) * ns])
+        e1.record(st)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / runs
+        q = pl.qp(sig, xs, pl.e_homo)
+        res[prop] = dict(ms_per_step=ms, value=units_per_step(cfg) / (ms * 1e-3), qp_eV=q['eps_qp'] * HA_EV)
+    pl.cheb_deg = cfg['cheb_deg']
+    return dict(value=res['split']['value'], ms_per_step=res['split']['ms_per_step'], samples=n,
+                qp_eV_split=round(res['split']['qp_eV'], 5), qp_eV_chebyshev=round(res['chebyshev']['qp_eV'], 5),
+                chebyshev_value_same_run=res['chebyshev']['value'])
+
+
 def split_study(cfg, pl, seed=77):
     """Plain propagation (no TDH feedback) of one TDH-sized batch by the split-operator scheme and
     by the degree-K Chebyshev step, on the pipeline's context (graph replay), timed with CUDA events."""
@@ -466,6 +494,7 @@ def split_study(cfg, pl, seed=77):
         err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
     return dict(unit=UNIT, vectors=B, split_value=out['split'], chebyshev_value=out['chebyshev'],
                 ratio=out['split'] / out['chebyshev'], rel_diff_after_20_steps=err,
+                pipeline=split_pipeline(cfg, pl),
                 note='propagation only (no TDH feedback); the split-operator step carries an O(dt^3) '
                      'splitting error, the degree-16 Chebyshev step is exact to rounding at this dt')
 
