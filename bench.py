@@ -531,6 +531,11 @@ def cv_study(args, cfg, pl, ks, base):
     sec = e0.elapsed_time(e1) * 1e-3
     S0, X0 = cv.plain_rows(Yp)
     r_pl = pl.qp(S0, X0, ks['e_homo'])
+    net_kept = cv.use_net
+    cv.use_net = False                    # the linear part alone, on the same rows
+    S2, X2 = cv.rows(Fc, Fp, Yp)
+    cv.use_net = net_kept
+    r_lin = pl.qp(S2, X2, ks['e_homo'])
     n = Yp.shape[0]
     per_sample_s = sec / n                 # paired samples plus their share of the cheap ones
     sd_pl, sd_cv = r_pl['se'] * HA_EV * n ** 0.5, r_cv['se'] * HA_EV * n ** 0.5
@@ -542,6 +547,7 @@ def cv_study(args, cfg, pl, ks, base):
                 qp_eV_plain=round(r_pl['eps_qp'] * HA_EV, 5), se_eV_plain=round(r_pl['se'] * HA_EV, 5),
                 qp_eV_cv=round(r_cv['eps_qp'] * HA_EV, 5), se_eV_cv=round(r_cv['se'] * HA_EV, 5),
                 variance_gain=round((r_pl['se'] / r_cv['se']) ** 2, 3),
+                variance_gain_linear_part_alone=round((r_pl['se'] / r_lin['se']) ** 2, 3), network_kept=bool(net_kept),
                 time_to_0_03eV_plain_s=round(t_plain, 1), time_to_0_03eV_cv_s=round(t_cv, 1),
                 time_to_0_03eV_cv_incl_training_s=round(t_cv + t_train, 1),
                 speedup=round(t_plain / t_cv, 3), speedup_incl_training=round(t_plain / (t_cv + t_train), 3))

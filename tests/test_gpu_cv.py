@@ -181,8 +181,17 @@ def test_control_variate_gain_tiny():
     plain = pl.qp(S0, X0, w[3])
     cvr = pl.qp(S1, X1, w[3])
     gain = (plain['se'] / cvr['se']) ** 2
-    print('control-variate gain (variance ratio) %.2f, QP plain %.4f +- %.4f eV, CV %.4f +- %.4f eV' % (
-        gain, plain['eps_qp'] * 27.2114, plain['se'] * 27.2114, cvr['eps_qp'] * 27.2114, cvr['se'] * 27.2114))
+    # the same rows with the linear part alone: what the trained network adds on top of it
+    net_kept = cv.use_net
+    cv.use_net = False
+    S2, X2 = cv.rows(Fc, Fp, Yp)
+    cv.use_net = net_kept
+    lin = pl.qp(S2, X2, w[3])
+    gain_lin = (plain['se'] / lin['se']) ** 2
+    print('control-variate gain (variance ratio) %.2f (linear part alone %.2f, network kept: %s), '
+          'QP plain %.4f +- %.4f eV, CV %.4f +- %.4f eV' % (
+              gain, gain_lin, net_kept, plain['eps_qp'] * 27.2114, plain['se'] * 27.2114,
+              cvr['eps_qp'] * 27.2114, cvr['se'] * 27.2114))
     assert abs(cvr['eps_qp'] - plain['eps_qp']) < 4 * plain['se']
     assert gain > 1.5
     # no cheap samples: the rows are the plain samples, bit for bit
