@@ -64,3 +64,12 @@ def test_gapped_coeffs_match_oracle(lib, N, eh, el):
     assert np.max(np.abs(a - ao)) < 1e-7
     xs = np.linspace(-1, 1, 2001)
     assert np.max(np.abs(cheb.cheb_scalar(a, xs) - cheb.cheb_scalar(ao, xs))) < 1e-6
+
+
+def test_control_variate_sizes_match_oracle(lib):
+    from oracle import mlp as omlp
+    for m2 in (1, 3, 10, 17):
+        assert sgw.sgw_cv_feature_count(m2) == omlp.feature_count(m2)
+        assert sgw.sgw_cv_shell_count(m2) == omlp.shell_count(m2)
+    assert sgw.sgw_cv_linear_size(20, 1603) == 2 * 20 + 1603 + 20 * 1603
+    assert sgw.sgw_cv_linear_size(0, 5) == 0
