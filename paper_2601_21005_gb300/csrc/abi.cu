@@ -1215,7 +1215,7 @@ sgw_status sgw_filter_occupied(sgw_ctx* ctx, const double* coeffs_host, int n_ch
     sgw_status s = check_ctx(ctx, true);
     if (s) return s;
     if (!ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
-    if (!coeffs_host || n_cheb < 0 || batch < 0 || batch > ctx->max_batch || !in_dev || !out_dev)
+    if (!coeffs_host || n_cheb < 0 || batch < 0 || batch > ctx->max_batch || (batch > 0 && (!in_dev || !out_dev)))
         return fail(ctx, SGW_EINVAL, "bad filter arguments");
     if (batch == 0) return SGW_OK;
     SGW_ALIGNED(ctx, in_dev, out_dev);
