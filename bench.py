@@ -383,8 +383,17 @@ def run_ours(args, cfg):
                h2d_bytes_per_step=phi_h.numel() * 4, d2h_bytes_per_step=sig_h.numel() * 16 + x_h.numel() * 8 + 32)
     # plain FP32 form (Sigma reductions, transform and QP in FP32) on the same samples as the
     # mixed form (FP64 there): the eV difference of the QP energy
-    prec = precision_comparison(cfg, sysd, ks, local, seed, pl, base)
+    prec = precision_comparison(cfg, pl, ks, base)
     cvres = cv_study(args, cfg, pl, ks, base) if args.cv > 0 else None
+    # the metric's comparison: time to +-0.03 eV of the chosen form (mixed precision + control
+    # variate) and of the plain FP32 form (no control variate, FP32 reductions at their own speed)
+    chosen = None
+    if cvres is not None:
+        plain_s = cvres['time_to_0_03eV_plain_s'] * prec['ms_per_step_plain_fp32'] / prec['ms_per_step_mixed']
+        chosen = dict(plain_fp32_seconds=round(plain_s, 1), chosen_seconds=cvres['time_to_0_03eV_cv_s'],
+                      chosen_seconds_incl_training=cvres['time_to_0_03eV_cv_incl_training_s'],
+                      speedup=round(plain_s / cvres['time_to_0_03eV_cv_s'], 3),
+                      speedup_incl_training=round(plain_s / cvres['time_to_0_03eV_cv_incl_training_s'], 3))
     split = split_study(cfg, pl)
     if rank != 0:
         if dist:
@@ -407,7 +416,8 @@ def run_ours(args, cfg):
                             roofline_timing='per-kernel CUDA events over the timed region' if not args.graphs else
                             'per-kernel CUDA events over one extra step (graph replay is timed unprofiled)'),
                 e2e=e2e, gpu_launches=int(launches), roofline=rl, cpu_baseline=cpu,
-                clocks=clk, time_to_0_03eV=tt, precision_forms=prec, control_variate=cvres, split_operator=split,
+                clocks=clk, time_to_0_03eV=tt, time_to_0_03eV_chosen_vs_plain=chosen, precision_forms=prec,
+                control_variate=cvres, split_operator=split,
                 setup=dict(seconds=round(t_setup, 2), e_homo=ks['e_homo'], e_lumo=ks['e_lumo'],
                            gap_eV=round((ks['e_lumo'] - ks['e_homo']) * HA_EV, 4), emin=ks['emin'], emax=ks['emax'],
                            eig_residual=float(ks['eig_residual'])))
@@ -416,23 +426,28 @@ def run_ours(args, cfg):
         dist.destroy_process_group()
 
 
-def precision_comparison(cfg, sysd, ks, device, seed, pl, base):
-    """Run one batch in the plain FP32 form and the same batch in the mixed form; QP difference."""
+def precision_comparison(cfg, pl, ks, base):
+    """The same step of samples in the mixed form (FP64 Sigma reductions, transform and QP) and in
+    the plain FP32 form, each timed with CUDA events after a warm-up run: QP difference and times."""
     import torch
-    # one chunk of samples in the plain form; the mixed pipeline runs its whole step on the same
-    # first samples (per-sample results do not depend on how samples are grouped)
-    pl32 = make_pipeline(cfg, sysd, ks, device, seed, fp64=False, zeta_group=1)
-    ns = cfg['samples_per_batch']
+    m = pl.run_samples
     out = {}
-    for name, p in (('mixed_fp64', pl), ('plain_fp32', pl32)):
-        m = p.run_samples
+    st = torch.cuda.current_stream()
+    for name, f in (('mixed_fp64', 1), ('plain_fp32', 0)):
+        pl.fp64 = f
         sg = torch.empty(m, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
         x = torch.empty(m, dtype=torch.float64, device='cuda')
-        p.run_batch(base + 900000, sg, x)
-        out[name] = p.qp(sg[:ns].contiguous(), x[:ns].contiguous(), ks['e_homo'])['eps_qp']
-    pl32.ctx.close()
-    return dict(qp_eV_mixed=round(out['mixed_fp64'] * HA_EV, 6), qp_eV_plain_fp32=round(out['plain_fp32'] * HA_EV, 6),
-                diff_eV=abs(out['plain_fp32'] - out['mixed_fp64']) * HA_EV, samples=ns)
+        pl.run_batch(base + 900000, sg, x)                   # warm-up (captures this form's graphs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        pl.run_batch(base + 900000, sg, x)
+        e1.record(st)
+        e1.synchronize()
+        out[name] = (pl.qp(sg, x, ks['e_homo'])['eps_qp'], e0.elapsed_time(e1))
+    pl.fp64 = 1
+    return dict(qp_eV_mixed=round(out['mixed_fp64'][0] * HA_EV, 6), qp_eV_plain_fp32=round(out['plain_fp32'][0] * HA_EV, 6),
+                diff_eV=abs(out['plain_fp32'][0] - out['mixed_fp64'][0]) * HA_EV, samples=m,
+                ms_per_step_mixed=round(out['mixed_fp64'][1], 1), ms_per_step_plain_fp32=round(out['plain_fp32'][1], 1))
 
 
 def split_pipeline(cfg, pl, runs=1):
