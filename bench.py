@@ -584,7 +584,8 @@ def main():
                     help='keep the default launch hints instead of timing the candidates at setup')
     ap.add_argument('--cv', type=int, default=128, help='control-variate training samples (0: skip the study)')
     ap.add_argument('--cv-cheap', type=int, default=4096, help='cheap (features-only) samples in the study')
-    ap.add_argument('--cv-paired-batches', type=int, default=2, help='runs of paired samples in the study')
+    ap.add_argument('--cv-paired-batches', type=int, default=4,
+                    help='runs of paired samples in the study (4 runs of 16: 64 paired corrections)')
     ap.add_argument('--scale', type=float, default=1.0,
                     help='scale N_tau and N_chb together (profiling captures of fewer launches)')
     args = ap.parse_args()
