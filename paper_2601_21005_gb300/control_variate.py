@@ -3,11 +3,12 @@
 A sample's Sigma_i(t) (Eq. 5) and its sROI exchange X_i (Eq. 6) are quadratic forms in the
 sample's random vectors (zeta-bar_i and the eta-bar_il), so cheap features of those vectors --
 the Coulomb-weighted low-k power of zeta-bar_i phi and of eta-bar_il phi, summed per |k| shell --
-predict part of them.  The predictor is f = (FP64 ridge-linear part) + (network on its residual).
+predict part of them.  The predictor is f = (FP64 ridge-linear part on the per-|k|-shell sums of the
+features) + (network on the per-k features, fitted to what the linear part leaves).
 The steps:
 
   collect : run plain samples (Pipeline.run_batch); targets Y_i = [Sigma_i(t) (2 (2N + 1) reals),
-            X_i], shell-summed features x_i of the same samples;
+            X_i], per-k features x_i of the same samples;
   train   : fit the linear part on the training samples (FP64 normal equations), then the
             network on the standardised residuals Y - f_lin(x) (GPU forward, backward, Adam),
             keeping the epoch with the lowest held-out loss -- and the network only if that
@@ -28,8 +29,8 @@ class ControlVariate:
         self.torch = torch
         self.pl = pipeline
         self.m2max = m2max
-        self.n_kfeat = _sgw.sgw_cv_feature_count(m2max)      # per-k features of the library
-        self.n_feat = _sgw.sgw_cv_shell_count(m2max)         # their shell sums: the model inputs
+        self.n_kfeat = _sgw.sgw_cv_feature_count(m2max)      # per-k features: the network's inputs
+        self.n_feat = _sgw.sgw_cv_shell_count(m2max)         # their shell sums: the linear part's inputs
         self.n_sig = 2 * (2 * pipeline.n_steps + 1)
         self.n_out = self.n_sig + 1
         self.max_batch = max_batch
@@ -37,7 +38,7 @@ class ControlVariate:
         self.lin = torch.zeros(_sgw.sgw_cv_linear_size(self.n_feat, self.n_out), dtype=torch.float64,
                                device=pipeline.dev)
         self.use_net = True
-        self.mlp = _sgw.MLP(self.n_feat, width, self.n_out, max_batch, seed=seed, device=pipeline.dev.index or 0,
+        self.mlp = _sgw.MLP(self.n_kfeat, width, self.n_out, max_batch, seed=seed, device=pipeline.dev.index or 0,
                             stream=pipeline.stream.cuda_stream if pipeline.stream is not None else None)
         # X is one output against 2 (2N + 1) for Sigma(t) but carries a comparable share of the
         # QP variance: give it half the weight of the whole Sigma block.
@@ -48,8 +49,8 @@ class ControlVariate:
         f64 = torch.float64
         self.mu = torch.zeros(self.n_out, dtype=f64, device=dev)
         self.sd = torch.ones(self.n_out, dtype=f64, device=dev)
-        self.mu_x = torch.zeros(self.n_feat, dtype=f64, device=dev)
-        self.sd_x = torch.ones(self.n_feat, dtype=f64, device=dev)
+        self.mu_x = torch.zeros(self.n_kfeat, dtype=f64, device=dev)
+        self.sd_x = torch.ones(self.n_kfeat, dtype=f64, device=dev)
         self._noise = None
 
     # -------------------------------------------------------------- data
@@ -58,7 +59,7 @@ class ControlVariate:
             return self._collect(n_samples, sample0)
 
     def _collect(self, n_samples, sample0):
-        """Plain samples sample0.. : (Y [n][n_out] f64 = [Sigma(t) interleaved, X], F [n][n_feat] f32)."""
+        """Plain samples sample0.. : (Y [n][n_out] f64 = [Sigma(t) interleaved, X], F [n][n_kfeat] f32)."""
         t, pl = self.torch, self.pl
         ns = pl.run_samples
         nb = (n_samples + ns - 1) // ns
@@ -77,7 +78,7 @@ class ControlVariate:
             return self._cheap_features(n_samples, sample0)
 
     def _cheap_features(self, n_samples, sample0):
-        """Features of samples sample0.. from their white noise alone (no filter, no propagation)."""
+        """Per-k features of samples sample0.. from their white noise alone (no filter, no propagation)."""
         t, pl = self.torch, self.pl
         nv = pl.n_eta + 1
         chunk = max(1, pl.ctx.max_batch // nv)
@@ -88,9 +89,13 @@ class ControlVariate:
             m = min(chunk, n_samples - s0)
             pl.ctx.white_noise(pl.seed, pl.stream_id, sample0 + s0, m, nv, self._noise)
             pl.ctx.cv_features(self._noise, m, nv, pl.phi, self.m2max, Fk[s0:s0 + m])
-        F = t.empty(n_samples, self.n_feat, dtype=t.float32, device=pl.dev)
-        pl.ctx.cv_shell_sums(Fk, self.m2max, F)
-        return F
+        return Fk
+
+    def _shells(self, F):
+        """Per-shell sums of per-k features (the linear part's inputs)."""
+        out = self.torch.empty(F.shape[0], self.n_feat, dtype=self.torch.float32, device=F.device)
+        self.pl.ctx.cv_shell_sums(F.contiguous(), self.m2max, out)
+        return out
 
     # -------------------------------------------------------------- network
     def train(self, F, Y, epochs=300, batch=64, lr=1e-3, holdout=0.2):
@@ -104,9 +109,10 @@ class ControlVariate:
         n = F.shape[0]
         nv = max(1, int(round(holdout * n))) if n > 4 else 0
         ntr = n - nv
-        ctx.cv_linear_fit(F[:ntr].contiguous(), Y[:ntr].contiguous(), self.ridge, self.lin)
+        Fs = self._shells(F)
+        ctx.cv_linear_fit(Fs[:ntr].contiguous(), Y[:ntr].contiguous(), self.ridge, self.lin)
         R = t.empty_like(Y)
-        ctx.cv_linear_apply(self.lin, F, self.n_out, R, y=Y)          # residuals Y - f_lin(x)
+        ctx.cv_linear_apply(self.lin, Fs, self.n_out, R, y=Y)         # residuals Y - f_lin(x)
         Y = R
         Fs = F.clone()
         ctx.cv_standardize_f32(Fs[:ntr], self.mu_x, self.sd_x, True)
@@ -168,7 +174,7 @@ class ControlVariate:
             self.pl.ctx.cv_rows(None, None, Y_paired, None, None, rows)
         else:
             Yl = t.empty_like(Y_paired)          # Y - f_lin(x_paired) + mean f_lin(x_cheap)
-            self.pl.ctx.cv_linear_rows(self.lin, F_cheap.contiguous(), F_paired.contiguous(), Y_paired, Yl)
+            self.pl.ctx.cv_linear_rows(self.lin, self._shells(F_cheap), self._shells(F_paired), Y_paired, Yl)
             if self.use_net:
                 self.pl.ctx.cv_rows(self._predict(F_cheap), self._predict(F_paired), Yl, self.mu, self.sd, rows)
             else:
