@@ -271,6 +271,34 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
 sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_samples,
                           int n_steps);
 
+/* The same time ordering for series of any length n_points per step ([n_samples][n_steps+1]
+ * [n_points]): used for the xi-compressed U_m(t) of sgw_tdh_response_xi (n_points = n_xi). */
+sgw_status sgw_time_order_points(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_samples, int n_steps,
+                                 int n_points);
+
+/*
+ * Sparse stochastic compression of u^R (Sec. 2.1 second paragraph, Sec. 2.3): instead of u^R on the
+ * full grid, carry U_m(t_j) = <xi_m|u^R(t_j)>, m < n_xi, for random functions xi_m on fragmented
+ * segments.  Reading of the construction: xi_m of MC sample (sample0 + s) is the sum of
+ * K = max(1, round(N_g f_g / L)) draws, draw k covering the L (<= 32, dividing N_g) contiguous flat
+ * grid points from L p with p = floor(w0 (N_g / L) / 2^32) and the sign of point l from bit l of w1
+ * (set -> -1), (w0, w1) = Philox4x32-10 words of counter (k, m, sample, xi_stream) and key xi_seed,
+ * times c = 1 / sqrt(n_xi K L dV / N_g), so that E[dV sum_m xi_m xi_m^T] = 1.
+ *  sgw_tdh_response_xi: as sgw_tdh_response, but writes U_dev [n_samples][n_steps+1][n_xi] float
+ *   (U_m(t_j) = dV sum_r xi_m(r) u^R(r, t_j)) instead of the full-grid u^R.  Time-order U with
+ *   sgw_time_order_points(..., n_points = n_xi).
+ *  sgw_sigma_c_xi: as sgw_sigma_c with u_dev [n_samples][n_steps+1][n_xi] c64 the time-ordered U:
+ *   Sigma(+-t_j) = +-sum_m U_m(t_j) dV sum_r phi zeta(r, +-t_j) xi_m(r).
+ * The same (xi_seed, xi_stream, sample0) must be passed to both.  SGW_EINVAL for n_xi < 1,
+ * f_g <= 0, L outside 1..32 or not dividing N_g, sample0 < 0.
+ */
+sgw_status sgw_tdh_response_xi(sgw_ctx* ctx, const void* eta_dev, const float* source_dev, int n_samples, int n_eta,
+                               int n_steps, double dt, int cheb_deg, double weight, uint64_t xi_seed,
+                               uint32_t xi_stream, int sample0, int n_xi, double f_g, int L, float* U_dev);
+sgw_status sgw_sigma_c_xi(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev, int n_samples,
+                          int n_steps, double dt, int cheb_deg, int fp64_accum, uint64_t xi_seed, uint32_t xi_stream,
+                          int sample0, int n_xi, double f_g, int L, double* sigma_dev);
+
 /*
  * zeta propagation and Sigma(t) (Eq. 4, Eq. 5): for each sample, zeta_unocc propagates
  * forward and zeta_occ backward under H0 for n_steps steps, and

@@ -1375,8 +1375,31 @@ sgw_status sgw_propagate_split(sgw_ctx* ctx, void* psi_dev, int batch, int n_ste
     });
 }
 
-sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* source_dev, int n_samples, int n_eta,
-                            int n_steps, double dt, int cheb_deg, double weight, float* uR_dev) {
+// The xi basis of a call: per-sample Philox draws (seed, stream, sample0 + s), K segment draws of L
+// points per function, scale c = 1 / sqrt(n_xi K L dV / N_g).
+struct XiArgs {
+    uint64_t seed;
+    uint32_t stream;
+    int sample0, n_xi, K, L;
+    double c;
+};
+
+static sgw_status xi_args(sgw_ctx* ctx, uint64_t seed, uint32_t stream, int sample0, int n_xi, double f_g, int L,
+                          XiArgs* xa) {
+    if (n_xi < 1 || !(f_g > 0.0) || L < 1 || L > 32 || ctx->ng % L != 0 || sample0 < 0)
+        return fail(ctx, SGW_EINVAL, "bad xi arguments (n_xi >= 1, f_g > 0, 1 <= L <= 32 dividing N_g)");
+    xa->seed = seed;
+    xa->stream = stream;
+    xa->sample0 = sample0;
+    xa->n_xi = n_xi;
+    xa->L = L;
+    xa->K = (int)std::max<long long>(1, std::llround((double)ctx->ng * f_g / L));
+    xa->c = 1.0 / std::sqrt((double)n_xi * xa->K * L * ctx->dV / (double)ctx->ng);
+    return SGW_OK;
+}
+
+static sgw_status tdh_run(sgw_ctx* ctx, const void* eta_dev, const float* source_dev, int n_samples, int n_eta,
+                          int n_steps, double dt, int cheb_deg, double weight, float* uR_dev, const XiArgs* xi) {
     sgw_status s = check_ctx(ctx, true);
     if (s) return s;
     if (cheb_deg > 0 && !ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
@@ -1423,6 +1446,10 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
     std::vector<uint64_t> key = {3, (uint64_t)n_samples, (uint64_t)n_eta, (uint64_t)n_steps, bits(dt),
                                  (uint64_t)cheb_deg, bits(w), (uint64_t)eta_dev, (uint64_t)source_dev, (uint64_t)uR_dev,
                                  (uint64_t)psi, (uint64_t)Wp, (uint64_t)vtot};
+    if (xi) {
+        key.insert(key.end(), {xi->seed, (uint64_t)xi->stream, (uint64_t)xi->sample0, (uint64_t)xi->n_xi,
+                               (uint64_t)xi->K, (uint64_t)xi->L});
+    }
     return graphed(ctx, key, [&]() -> sgw_status {
         // v_p = v_C * source (Poisson, periodic, k = 0 dropped)
         {
@@ -1448,7 +1475,14 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
             {
                 Launch L(ctx, SGW_PROF_OTHER);
                 sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 1, nullptr, ctx->vloc, vtot, dv,
-                                      uR_dev + (int64_t)j * ng, uR_stride, nullptr, st);
+                                      xi ? nullptr : uR_dev + (int64_t)j * ng, uR_stride, nullptr, st);
+            }
+            if (xi) {
+                // U_m(t_j) = <xi_m|u^R(t_j)>, u^R(t_j) = dv: the full-grid u^R is not kept
+                Launch L(ctx, SGW_PROF_OTHER, 1, (double)xi->n_xi * xi->K * xi->L * 4.0 * n_samples);
+                sgw::launch_xi_project(dv, ng, n_samples, xi->n_xi, xi->K, xi->L, ng, xi->seed, xi->stream, xi->sample0,
+                                       (float)(xi->c * ctx->dV), uR_dev + (int64_t)j * xi->n_xi,
+                                       (int64_t)(n_steps + 1) * xi->n_xi, st);
             }
             CKL();
             if (j == n_steps) break;
@@ -1462,10 +1496,31 @@ sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* sour
     });
 }
 
+sgw_status sgw_tdh_response(sgw_ctx* ctx, const void* eta_dev, const float* source_dev, int n_samples, int n_eta,
+                            int n_steps, double dt, int cheb_deg, double weight, float* uR_dev) {
+    return tdh_run(ctx, eta_dev, source_dev, n_samples, n_eta, n_steps, dt, cheb_deg, weight, uR_dev, nullptr);
+}
+
+sgw_status sgw_tdh_response_xi(sgw_ctx* ctx, const void* eta_dev, const float* source_dev, int n_samples, int n_eta,
+                               int n_steps, double dt, int cheb_deg, double weight, uint64_t xi_seed,
+                               uint32_t xi_stream, int sample0, int n_xi, double f_g, int L, float* U_dev) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    XiArgs xa;
+    if ((s = xi_args(ctx, xi_seed, xi_stream, sample0, n_xi, f_g, L, &xa))) return s;
+    return tdh_run(ctx, eta_dev, source_dev, n_samples, n_eta, n_steps, dt, cheb_deg, weight, U_dev, &xa);
+}
+
 sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_samples, int n_steps) {
+    if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
+    return sgw_time_order_points(ctx, uR_dev, u_dev, n_samples, n_steps, (int)ctx->ng);
+}
+
+sgw_status sgw_time_order_points(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_samples, int n_steps,
+                                 int n_points) {
     sgw_status s = check_ctx(ctx, false);
     if (s) return s;
-    if (n_samples < 0 || n_steps < 0) return fail(ctx, SGW_EINVAL, "bad time-order arguments");
+    if (n_samples < 0 || n_steps < 0 || n_points < 1) return fail(ctx, SGW_EINVAL, "bad time-order arguments");
     if (n_samples == 0) return SGW_OK;
     if (!uR_dev || !u_dev) return fail(ctx, SGW_EINVAL, "null time-order pointers");
     SGW_ALIGNED(ctx, uR_dev, u_dev);
@@ -1482,15 +1537,15 @@ sgw_status sgw_time_order(sgw_ctx* ctx, const float* uR_dev, void* u_dev, int n_
         ctx->twM_n = M;
     }
     {
-        Launch L(ctx, SGW_PROF_TIME_ORDER, 1, (double)ctx->ng * n_samples * (n_steps + 1) * 12.0);
-        sgw::launch_time_order((int)ctx->ng, uR_dev, (float2*)u_dev, n_samples, n_steps, M, ctx->twM, ctx->stream);
+        Launch L(ctx, SGW_PROF_TIME_ORDER, 1, (double)n_points * n_samples * (n_steps + 1) * 12.0);
+        sgw::launch_time_order(n_points, uR_dev, (float2*)u_dev, n_samples, n_steps, M, ctx->twM, ctx->stream);
         CKL();
     }
     return SGW_OK;
 }
 
-sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev, int n_samples, int n_steps,
-                       double dt, int cheb_deg, int fp64_accum, double* sigma_dev) {
+static sgw_status sigma_run(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev, int n_samples,
+                            int n_steps, double dt, int cheb_deg, int fp64_accum, double* sigma_dev, const XiArgs* xi) {
     sgw_status s = check_ctx(ctx, true);
     if (s) return s;
     if (cheb_deg > 0 && !ctx->have_spectrum) return fail(ctx, SGW_ESTATE, "no spectral interval set");
@@ -1502,7 +1557,7 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
     cudaStream_t st = ctx->stream;
     const int64_t ng = ctx->ng;
     const int B = 2 * n_samples;
-    const int nblk = (int)std::min<int64_t>((ng + 255) / 256, 128);
+    const int nblk = xi ? (int)std::min<int64_t>((xi->n_xi + 7) / 8, 128) : (int)std::min<int64_t>((ng + 255) / 256, 128);
     void* p;
     if ((s = work(ctx, 4, sizeof(double2) * (size_t)n_samples * (n_steps + 1) * 2 * nblk, &p))) return s;
     double2* partial = (double2*)p;
@@ -1523,16 +1578,28 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
     }
     if ((s = upload_info(ctx, info))) return s;
     float2* z = (float2*)zeta_dev;
-    const int64_t u_ss = (int64_t)(n_steps + 1) * ng;
+    const int64_t u_ss = (int64_t)(n_steps + 1) * (xi ? xi->n_xi : ng);
     std::vector<uint64_t> key = {4, (uint64_t)n_samples, (uint64_t)n_steps, bits(dt), (uint64_t)cheb_deg,
                                  (uint64_t)fp64_accum, (uint64_t)zeta_dev, (uint64_t)phi_dev, (uint64_t)u_dev,
                                  (uint64_t)sigma_dev, (uint64_t)partial};
+    if (xi) {
+        key.insert(key.end(), {xi->seed, (uint64_t)xi->stream, (uint64_t)xi->sample0, (uint64_t)xi->n_xi,
+                               (uint64_t)xi->K, (uint64_t)xi->L});
+    }
     return graphed(ctx, key, [&]() -> sgw_status {
     for (int j = 0; j <= n_steps; ++j) {
         {
-            Launch L(ctx, SGW_PROF_SIGMA, 1, (double)ng * n_samples * (8.0 * 3 + 4.0));
-            sgw::launch_sigma_accum((int)ng, z, phi_dev, (const float2*)u_dev, n_samples, u_ss, j, n_steps,
-                                    (float)ctx->dV, fp64_accum, partial, nblk, st);
+            if (xi) {
+                Launch L(ctx, SGW_PROF_SIGMA, 1,
+                         (double)xi->n_xi * xi->K * xi->L * n_samples * (8.0 * 2 + 4.0) + 8.0 * xi->n_xi * n_samples);
+                sgw::launch_sigma_accum_xi(z, phi_dev, (const float2*)u_dev, n_samples, u_ss, j, n_steps, xi->n_xi,
+                                           xi->K, xi->L, ng, xi->seed, xi->stream, xi->sample0, (float)xi->c, fp64_accum,
+                                           partial, nblk, st);
+            } else {
+                Launch L(ctx, SGW_PROF_SIGMA, 1, (double)ng * n_samples * (8.0 * 3 + 4.0));
+                sgw::launch_sigma_accum((int)ng, z, phi_dev, (const float2*)u_dev, n_samples, u_ss, j, n_steps,
+                                        (float)ctx->dV, fp64_accum, partial, nblk, st);
+            }
             CKL();
         }
         if (j == n_steps) break;
@@ -1550,6 +1617,21 @@ sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const
     }
     return SGW_OK;
     });
+}
+
+sgw_status sgw_sigma_c(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev, int n_samples, int n_steps,
+                       double dt, int cheb_deg, int fp64_accum, double* sigma_dev) {
+    return sigma_run(ctx, zeta_dev, phi_dev, u_dev, n_samples, n_steps, dt, cheb_deg, fp64_accum, sigma_dev, nullptr);
+}
+
+sgw_status sgw_sigma_c_xi(sgw_ctx* ctx, void* zeta_dev, const float* phi_dev, const void* u_dev, int n_samples,
+                          int n_steps, double dt, int cheb_deg, int fp64_accum, uint64_t xi_seed, uint32_t xi_stream,
+                          int sample0, int n_xi, double f_g, int L, double* sigma_dev) {
+    sgw_status s = check_ctx(ctx, true);
+    if (s) return s;
+    XiArgs xa;
+    if ((s = xi_args(ctx, xi_seed, xi_stream, sample0, n_xi, f_g, L, &xa))) return s;
+    return sigma_run(ctx, zeta_dev, phi_dev, u_dev, n_samples, n_steps, dt, cheb_deg, fp64_accum, sigma_dev, &xa);
 }
 
 sgw_status sgw_exchange(sgw_ctx* ctx, const void* eta_dev, const float* phi_dev, int n_samples, int n_eta,

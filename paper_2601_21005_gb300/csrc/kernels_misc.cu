@@ -267,6 +267,111 @@ void launch_sigma_accum(int ng, const float2* zeta, const float* phi, const floa
         k_sigma_accum<float><<<grid, 256, 0, st>>>(ng, zeta, phi, u, u_sample_stride, j, n_steps, partial);
 }
 
+// ------------------------------------------------------------------ xi compression (Sec. 2.3)
+// Draw k of xi_m of sample `sample`: Philox counter (k, m, sample, stream): segment p = floor(w0
+// n_seg / 2^32) (the L points from L p), sign of point l = bit l of w1 (set -> -1).
+__device__ __forceinline__ void xi_draw(uint32_t k, uint32_t m, uint32_t sample, uint32_t stream, uint32_t k0,
+                                        uint32_t k1, uint32_t n_seg, uint32_t* pos, uint32_t* signs) {
+    const uint4 w = philox4x32_10(make_uint4(k, m, sample, stream), k0, k1);
+    *pos = (uint32_t)(((uint64_t)w.x * n_seg) >> 32);
+    *signs = w.y;
+}
+
+// U[s][m] (row stride u_ss per sample) = c dV sum_r xi_m(r) f_s(r) for real rows f_s (stride f_ss):
+// one warp per (m, s), lane l < L on point l of each draw; warp sums in a fixed order.
+__global__ void __launch_bounds__(256)
+k_xi_project(const float* __restrict__ f, int64_t f_ss, int n_samples, int n_xi, int K, int L, uint32_t n_seg,
+             uint32_t k0, uint32_t k1, uint32_t stream, int sample0, float cdv, float* __restrict__ U, int64_t u_ss) {
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= (int64_t)n_xi * n_samples) return;
+    const int m = (int)(w % n_xi), s = (int)(w / n_xi);
+    const float* fs = f + (size_t)s * f_ss;
+    float acc = 0.f;
+    for (int k = 0; k < K; ++k) {
+        uint32_t p, sg;
+        xi_draw((uint32_t)k, (uint32_t)m, (uint32_t)(sample0 + s), stream, k0, k1, n_seg, &p, &sg);
+        if (lane < L) {
+            const float v = fs[(size_t)p * L + lane];
+            acc += ((sg >> lane) & 1u) ? -v : v;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) U[(size_t)s * u_ss + m] = cdv * acc;
+}
+
+void launch_xi_project(const float* f, int64_t f_ss, int n_samples, int n_xi, int K, int L, int64_t ng, uint64_t seed,
+                       uint32_t stream, int sample0, float cdv, float* U, int64_t u_ss, cudaStream_t st) {
+    const int64_t warps = (int64_t)n_xi * n_samples;
+    if (warps == 0) return;
+    k_xi_project<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+        f, f_ss, n_samples, n_xi, K, L, (uint32_t)(ng / L), (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32),
+        stream, sample0, cdv, U, u_ss);
+}
+
+// Sigma accumulation in the xi basis: partial sums of sum_m U_m(j) c sum_r xi_m(r)... written as
+// sum_m U_m(j) [c sum_k sum_l sign phi zeta] for zeta_unocc (pm 0) and zeta_occ (pm 1), same partial
+// layout as k_sigma_accum (the dV and the signs of Sigma(-t) are applied by k_sigma_reduce).
+// Block b of sample s takes xi functions m = warp index + b * warps_per_block, strided by the grid.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_sigma_accum_xi(const float2* __restrict__ zeta, const float* __restrict__ phi, const float2* __restrict__ Uxi,
+                 int64_t u_ss, int j, int n_steps, int n_xi, int K, int L, uint32_t n_seg, uint32_t k0, uint32_t k1,
+                 uint32_t stream, int sample0, float c, int64_t ng, double2* __restrict__ partial) {
+    __shared__ T sh[32 * 4];
+    const int s = blockIdx.y;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    const float2* zo = zeta + (size_t)(2 * s) * ng;
+    const float2* zu = zeta + (size_t)(2 * s + 1) * ng;
+    const float2* Uj = Uxi + (size_t)s * u_ss + (size_t)j * n_xi;
+    T a[4] = {0, 0, 0, 0};
+    for (int m = blockIdx.x * wpb + wib; m < n_xi; m += gridDim.x * wpb) {
+        float b[4] = {0.f, 0.f, 0.f, 0.f};     // sum over the support of sign phi zeta_unocc / zeta_occ
+        for (int k = 0; k < K; ++k) {
+            uint32_t p, sg;
+            xi_draw((uint32_t)k, (uint32_t)m, (uint32_t)(sample0 + s), stream, k0, k1, n_seg, &p, &sg);
+            if (lane < L) {
+                const size_t r = (size_t)p * L + lane;
+                const float f = ((sg >> lane) & 1u) ? -phi[r] : phi[r];
+                const float2 pu = zu[r], po = zo[r];
+                b[0] += f * pu.x; b[1] += f * pu.y;
+                b[2] += f * po.x; b[3] += f * po.y;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            for (int o = 16; o > 0; o >>= 1) b[i] += __shfl_xor_sync(0xffffffffu, b[i], o);
+        if (lane == 0) {
+            const float2 u = Uj[m];
+            const T ur = (T)u.x * c, ui = (T)u.y * c;
+            a[0] += (T)b[0] * ur - (T)b[1] * ui;
+            a[1] += (T)b[0] * ui + (T)b[1] * ur;
+            a[2] += (T)b[2] * ur - (T)b[3] * ui;
+            a[3] += (T)b[2] * ui + (T)b[3] * ur;
+        }
+    }
+    if constexpr (sizeof(T) == 8) block_sum<4>(a, sh);
+    else block_sumf<4>(a, sh);
+    if (threadIdx.x == 0) {
+        const size_t base = ((size_t)s * (n_steps + 1) + j) * 2;
+        partial[(base + 0) * gridDim.x + blockIdx.x] = make_double2((double)a[0], (double)a[1]);
+        partial[(base + 1) * gridDim.x + blockIdx.x] = make_double2((double)a[2], (double)a[3]);
+    }
+}
+
+void launch_sigma_accum_xi(const float2* zeta, const float* phi, const float2* Uxi, int n_samples, int64_t u_ss, int j,
+                           int n_steps, int n_xi, int K, int L, int64_t ng, uint64_t seed, uint32_t stream, int sample0,
+                           float c, int fp64, double2* partial, int nblk, cudaStream_t st) {
+    const dim3 grid(nblk, n_samples);
+    const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32), ns = (uint32_t)(ng / L);
+    if (fp64)
+        k_sigma_accum_xi<double><<<grid, 256, 0, st>>>(zeta, phi, Uxi, u_ss, j, n_steps, n_xi, K, L, ns, k0, k1, stream,
+                                                       sample0, c, ng, partial);
+    else
+        k_sigma_accum_xi<float><<<grid, 256, 0, st>>>(zeta, phi, Uxi, u_ss, j, n_steps, n_xi, K, L, ns, k0, k1, stream,
+                                                      sample0, c, ng, partial);
+}
+
 // sigma[s][n + j] = dV S+ ; sigma[s][n - j] = -dV S- ; sigma[s][n] = (dV S+ - dV S-)/2 at j = 0.
 // The cross-block sums run in the accumulation precision (fp64 flag).
 __global__ void k_sigma_reduce(const double2* __restrict__ partial, int n_samples, int n_steps, int nblk, double dV,

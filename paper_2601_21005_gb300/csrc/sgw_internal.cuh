@@ -139,6 +139,11 @@ void launch_power_update(int ng, const float2* w, float2* v, const double* scal,
 void launch_sigma_accum(int ng, const float2* zeta, const float* phi, const float2* u, int n_samples,
                         int64_t u_sample_stride, int j, int n_steps, float dV, int fp64, double2* partial,
                         int nblk, cudaStream_t st);
+void launch_xi_project(const float* f, int64_t f_ss, int n_samples, int n_xi, int K, int L, int64_t ng, uint64_t seed,
+                       uint32_t stream, int sample0, float cdv, float* U, int64_t u_ss, cudaStream_t st);
+void launch_sigma_accum_xi(const float2* zeta, const float* phi, const float2* Uxi, int n_samples, int64_t u_ss, int j,
+                           int n_steps, int n_xi, int K, int L, int64_t ng, uint64_t seed, uint32_t stream, int sample0,
+                           float c, int fp64, double2* partial, int nblk, cudaStream_t st);
 void launch_sigma_reduce(const double2* partial, int n_samples, int n_steps, int nblk, double dV, int fp64,
                          double* sigma, cudaStream_t st);
 void launch_time_order(int ng, const float* uR, float2* u, int n_samples, int n_steps, int M,

@@ -52,6 +52,11 @@ _SIGS = {
     'sgw_propagate_split': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _P], _c.c_int),
     'sgw_tdh_response': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_double, _P], _c.c_int),
     'sgw_time_order': ([_P, _P, _P, _c.c_int, _c.c_int], _c.c_int),
+    'sgw_time_order_points': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_int], _c.c_int),
+    'sgw_tdh_response_xi': ([_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_double,
+                             _c.c_uint64, _c.c_uint32, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _P], _c.c_int),
+    'sgw_sigma_c_xi': ([_P, _P, _P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_int, _c.c_uint64,
+                        _c.c_uint32, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _P], _c.c_int),
     'sgw_sigma_c': ([_P, _P, _P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_exchange': ([_P, _P, _P, _c.c_int, _c.c_int, _P], _c.c_int),
     'sgw_sigma_omega': ([_P, _P, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _P, _c.c_int, _c.c_int, _P], _c.c_int),
@@ -380,6 +385,27 @@ class Context:
         self._ck('sgw_tdh_response', lib().sgw_tdh_response(self._p, _dev(eta, torch.complex64),
                                                            _dev(source, torch.float32), n_samples, n_eta, n_steps, dt,
                                                            cheb_deg, weight, _dev(uR, torch.float32)))
+
+    def time_order_points(self, uR, u, n_samples, n_steps, n_points):
+        import torch
+        self._ck('sgw_time_order_points', lib().sgw_time_order_points(self._p, _dev(uR, torch.float32),
+                                                                     _dev(u, torch.complex64), n_samples, n_steps,
+                                                                     n_points))
+
+    def tdh_response_xi(self, eta, source, n_samples, n_eta, n_steps, dt, cheb_deg, xi, U, weight=0.0):
+        """xi = (seed, stream, sample0, n_xi, f_g, L); U [n_samples][n_steps + 1][n_xi] float."""
+        import torch
+        seed, stream, sample0, n_xi, f_g, L = xi
+        self._ck('sgw_tdh_response_xi', lib().sgw_tdh_response_xi(
+            self._p, _dev(eta, torch.complex64), _dev(source, torch.float32), n_samples, n_eta, n_steps, dt,
+            cheb_deg, weight, seed, stream, sample0, n_xi, f_g, L, _dev(U, torch.float32)))
+
+    def sigma_c_xi(self, zeta, phi, u, n_samples, n_steps, dt, cheb_deg, xi, sigma, fp64_accum=1):
+        import torch
+        seed, stream, sample0, n_xi, f_g, L = xi
+        self._ck('sgw_sigma_c_xi', lib().sgw_sigma_c_xi(
+            self._p, _dev(zeta, torch.complex64), _dev(phi, torch.float32), _dev(u, torch.complex64), n_samples,
+            n_steps, dt, cheb_deg, fp64_accum, seed, stream, sample0, n_xi, f_g, L, _dev(sigma, torch.complex128)))
 
     def time_order(self, uR, u, n_samples, n_steps):
         import torch
