@@ -395,6 +395,7 @@ def run_ours(args, cfg):
                       speedup=round(plain_s / cvres['time_to_0_03eV_cv_s'], 3),
                       speedup_incl_training=round(plain_s / cvres['time_to_0_03eV_cv_incl_training_s'], 3))
     split = split_study(cfg, pl)
+    xis = xi_study(args, cfg, sysd, ks, pl, base) if args.xi else None
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -417,7 +418,7 @@ def run_ours(args, cfg):
                             'per-kernel CUDA events over one extra step (graph replay is timed unprofiled)'),
                 e2e=e2e, gpu_launches=int(launches), roofline=rl, cpu_baseline=cpu,
                 clocks=clk, time_to_0_03eV=tt, time_to_0_03eV_chosen_vs_plain=chosen, precision_forms=prec,
-                control_variate=cvres, split_operator=split,
+                control_variate=cvres, split_operator=split, xi_compression=xis,
                 setup=dict(seconds=round(t_setup, 2), e_homo=ks['e_homo'], e_lumo=ks['e_lumo'],
                            gap_eV=round((ks['e_lumo'] - ks['e_homo']) * HA_EV, 4), emin=ks['emin'], emax=ks['emax'],
                            eig_residual=float(ks['eig_residual'])))
@@ -514,6 +515,58 @@ def split_study(cfg, pl, seed=77):
                      'splitting error, the degree-16 Chebyshev step is exact to rounding at this dt')
 
 
+def xi_study(args, cfg, sysd, ks, pl, base, n_xi=10000, f_g=0.003, L=32):
+    """The same samples through the full-grid pipeline and through one that carries u^R in the sparse
+    stochastic xi basis (n_xi functions of grid fraction f_g in segments of L points, the sizes of the
+    paper's runs), each timed with CUDA events after a warm-up run: time per step, bytes of the stored
+    u, and the spread the xi projection adds to the per-sample Re Sigma_i(eps_KS) against the Monte-Carlo
+    spread of the full-grid values."""
+    import numpy as np
+    import torch
+    from paper_2601_21005_gb300.pipeline import Pipeline
+    pxi = Pipeline(cfg['n'], cfg['h'], sysd['vloc'], sysd['kb_atoms'], ks['phi'], ks['e_homo'], ks['e_lumo'],
+                   n_eta=cfg['n_eta'], n_steps=cfg['n_steps'], dt=cfg['dt'], cheb_deg=cfg['cheb_deg'],
+                   n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'], seed=pl.seed, stream_id=1,
+                   device=pl.dev.index, spectrum=(ks['emin'], ks['emax']), graphs=args.graphs,
+                   zeta_group=cfg['zeta_group'], xi=dict(n_xi=n_xi, f_g=f_g, L=L))
+    if pl.tuning:
+        for key, v in enumerate(pl.tuning):
+            pxi.ctx.set_tuning(key, v)
+    m = pl.run_samples
+    N = cfg['n_steps']
+    res = {}
+    for name, p in (('full_grid', pl), ('xi', pxi)):
+        sg = torch.empty(m, 2 * N + 1, dtype=torch.complex128, device='cuda')
+        x = torch.empty(m, dtype=torch.float64, device='cuda')
+        p.run_batch(base + 700000, sg, x)                  # warm-up (graph capture)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        p.run_batch(base + 700000, sg, x)
+        e1.record(st)
+        e1.synchronize()
+        om = torch.tensor([ks['e_homo']], dtype=torch.float64, device='cuda')
+        per = []
+        for i in range(m):
+            o = torch.empty(1, dtype=torch.complex128, device='cuda')
+            p.ctx.sigma_omega(sg[i:i + 1].contiguous(), 1, N, cfg['dt'], p.gamma, om, o)
+            per.append(float(o.real.item()))
+        res[name] = dict(ms=e0.elapsed_time(e1), per=np.array(per), qp=p.qp(sg, x, ks['e_homo'])['eps_qp'],
+                         u_bytes=p.u.numel() * p.u.element_size() + p.uR.numel() * p.uR.element_size())
+    pxi.ctx.close()
+    d = res['xi']['per'] - res['full_grid']['per']
+    sd_full = float(res['full_grid']['per'].std(ddof=1))
+    return dict(n_xi=n_xi, f_g=f_g, L=L, samples=m,
+                ms_per_step_full_grid=round(res['full_grid']['ms'], 1), ms_per_step_xi=round(res['xi']['ms'], 1),
+                u_bytes_full_grid=int(res['full_grid']['u_bytes']), u_bytes_xi=int(res['xi']['u_bytes']),
+                qp_eV_full_grid=round(res['full_grid']['qp'] * HA_EV, 5), qp_eV_xi=round(res['xi']['qp'] * HA_EV, 5),
+                re_sigma_sd_eV_full_grid=round(sd_full * HA_EV, 5),
+                re_sigma_sd_eV_xi_minus_full=round(float(d.std(ddof=1)) * HA_EV, 5),
+                added_variance_ratio=round(float(d.var(ddof=1)) / max(sd_full ** 2, 1e-300), 4),
+                note='per-sample Re Sigma_i(eps_KS); the xi form is unbiased over the xi draws, so its added '
+                     'variance adds to the Monte-Carlo variance of the same samples')
+
+
 def cv_study(args, cfg, pl, ks, base):
     """Train the control variate on args.cv plain samples, then time steps of the chosen form
     (one batch of paired samples plus cheap samples per step) against the plain estimator on the
@@ -582,6 +635,7 @@ def main():
                     help='launch every kernel directly instead of replaying the loops as CUDA graphs')
     ap.add_argument('--no-autotune', dest='autotune', action='store_false',
                     help='keep the default launch hints instead of timing the candidates at setup')
+    ap.add_argument('--no-xi', dest='xi', action='store_false', help='skip the xi-compression study')
     ap.add_argument('--cv', type=int, default=128, help='control-variate training samples (0: skip the study)')
     ap.add_argument('--cv-cheap', type=int, default=4096, help='cheap (features-only) samples in the study')
     ap.add_argument('--cv-paired-batches', type=int, default=4,

@@ -288,12 +288,17 @@ k_xi_project(const float* __restrict__ f, int64_t f_ss, int n_samples, int n_xi,
     const int m = (int)(w % n_xi), s = (int)(w / n_xi);
     const float* fs = f + (size_t)s * f_ss;
     float acc = 0.f;
-    for (int k = 0; k < K; ++k) {
-        uint32_t p, sg;
-        xi_draw((uint32_t)k, (uint32_t)m, (uint32_t)(sample0 + s), stream, k0, k1, n_seg, &p, &sg);
-        if (lane < L) {
-            const float v = fs[(size_t)p * L + lane];
-            acc += ((sg >> lane) & 1u) ? -v : v;
+    for (int kb = 0; kb < K; kb += 32) {
+        // lane i draws segment kb + i once; the warp walks the draws in order through shuffles
+        uint32_t pl = 0, sgl = 0;
+        if (kb + lane < K) xi_draw((uint32_t)(kb + lane), (uint32_t)m, (uint32_t)(sample0 + s), stream, k0, k1, n_seg, &pl, &sgl);
+        const int kn = min(32, K - kb);
+        for (int i = 0; i < kn; ++i) {
+            const uint32_t p = __shfl_sync(0xffffffffu, pl, i), sg = __shfl_sync(0xffffffffu, sgl, i);
+            if (lane < L) {
+                const float v = fs[(size_t)p * L + lane];
+                acc += ((sg >> lane) & 1u) ? -v : v;
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -327,15 +332,20 @@ k_sigma_accum_xi(const float2* __restrict__ zeta, const float* __restrict__ phi,
     T a[4] = {0, 0, 0, 0};
     for (int m = blockIdx.x * wpb + wib; m < n_xi; m += gridDim.x * wpb) {
         float b[4] = {0.f, 0.f, 0.f, 0.f};     // sum over the support of sign phi zeta_unocc / zeta_occ
-        for (int k = 0; k < K; ++k) {
-            uint32_t p, sg;
-            xi_draw((uint32_t)k, (uint32_t)m, (uint32_t)(sample0 + s), stream, k0, k1, n_seg, &p, &sg);
-            if (lane < L) {
-                const size_t r = (size_t)p * L + lane;
-                const float f = ((sg >> lane) & 1u) ? -phi[r] : phi[r];
-                const float2 pu = zu[r], po = zo[r];
-                b[0] += f * pu.x; b[1] += f * pu.y;
-                b[2] += f * po.x; b[3] += f * po.y;
+        for (int kb = 0; kb < K; kb += 32) {
+            uint32_t pl = 0, sgl = 0;
+            if (kb + lane < K)
+                xi_draw((uint32_t)(kb + lane), (uint32_t)m, (uint32_t)(sample0 + s), stream, k0, k1, n_seg, &pl, &sgl);
+            const int kn = min(32, K - kb);
+            for (int i = 0; i < kn; ++i) {
+                const uint32_t p = __shfl_sync(0xffffffffu, pl, i), sg = __shfl_sync(0xffffffffu, sgl, i);
+                if (lane < L) {
+                    const size_t r = (size_t)p * L + lane;
+                    const float f = ((sg >> lane) & 1u) ? -phi[r] : phi[r];
+                    const float2 pu = zu[r], po = zo[r];
+                    b[0] += f * pu.x; b[1] += f * pu.y;
+                    b[2] += f * po.x; b[3] += f * po.y;
+                }
             }
         }
 #pragma unroll

@@ -7,6 +7,12 @@ libsgw; torch only allocates the device buffers and streams:
   exchange X (Eq. 6) -> linear-response TDH u^R(t) -> time ordering u(t) ->
   zeta propagation with Sigma(t) accumulation (Eq. 4, 5) -> ... over batches ... ->
   Sigma(omega) (Eq. 7) and the QP root (Eq. 6) on the sample means.
+
+With xi=dict(n_xi=.., f_g=.., L=..) u^R(t) is carried as its overlaps U_m(t) = <xi_m|u^R(t)> with
+n_xi sparse random functions on fragmented segments (Sec. 2.1, Sec. 2.3): u is stored as
+[samples][N+1][n_xi] instead of [samples][N+1][N_g], the time ordering acts on U_m, and Sigma(t)
+is accumulated in the xi basis.  The xi draws of sample i use the pipeline's seed, the counter
+stream xi['stream'] (default stream_id + 2^16) and the global sample index i.
 """
 import contextlib
 
@@ -19,7 +25,7 @@ class Pipeline:
     def __init__(self, n, h, vloc, kb_atoms, phi, e_homo, e_lumo, n_eta=8, n_steps=200, dt=0.05,
                  cheb_deg=16, n_cheb=128, samples_per_batch=1, seed=1000, stream_id=1, device=0, ecut=0.0,
                  spectrum=None, coeffs=None, bounds_iter=100, margin=0.05, fp64=True, stream=None, graphs=False,
-                 autotune=False, zeta_group=1, propagator='chebyshev'):
+                 autotune=False, zeta_group=1, propagator='chebyshev', xi=None):
         import torch
         self.torch = torch
         # CUDA graphs need a non-default stream: the pipeline then owns one, and its buffers are
@@ -35,10 +41,12 @@ class Pipeline:
         self.propagator = propagator
         self.n_eta, self.n_steps, self.dt = n_eta, n_steps, dt
         self.cheb_deg = 0 if propagator == 'split' else cheb_deg
-        # a run is zeta_group chunks of samples_per_batch samples: white noise, filter, exchange, TDH and
-        # time ordering chunk by chunk (2 N_eta samples_per_batch TDH orbitals per launch), then the
-        # zeta pairs of all the run's samples in one propagation (2 samples_per_batch zeta_group
-        # vectors per launch), with u of every sample of the run kept in HBM
+        # a run is zeta_group chunks of samples_per_batch samples: white noise and the occupied filter
+        # for all the run's samples at once ((N_eta + 1) samples_per_batch zeta_group vectors per
+        # launch), exchange, TDH and time ordering chunk by chunk (2 N_eta samples_per_batch TDH
+        # orbitals per launch), then the zeta pairs of all the run's samples in one propagation
+        # (2 samples_per_batch zeta_group vectors per launch), with u of every sample of the run kept
+        # in HBM
         self.ns = samples_per_batch
         self.group = int(zeta_group)
         if self.group < 1:
@@ -47,7 +55,7 @@ class Pipeline:
         self.seed, self.stream_id = seed, stream_id
         self.fp64 = 1 if fp64 else 0
         self.dev = torch.device('cuda', device)
-        mb = max(self.ns * (n_eta + 1), 2 * self.ns * n_eta, 2 * self.run_samples)
+        mb = max(self.run_samples * (n_eta + 1), 2 * self.ns * n_eta, 2 * self.run_samples)
         self.ctx = _sgw.Context(n, h, ecut=ecut, max_batch=mb, device=device, stream=stream)
         if graphs:
             self.ctx.set_graph_mode(True)
@@ -67,13 +75,24 @@ class Pipeline:
         self.phi = torch.as_tensor(np.asarray(phi, dtype=np.float32).reshape(-1)).to(self.dev)
         ng, ns, N = self.ng, self.ns, n_steps
         c64, f32 = torch.complex64, torch.float32
-        self.noise = torch.empty(ns * (n_eta + 1), ng, dtype=c64, device=self.dev)
+        self.noise = torch.empty(self.run_samples * (n_eta + 1), ng, dtype=c64, device=self.dev)
         self.filt = torch.empty_like(self.noise)
         self.eta = torch.empty(ns * n_eta, ng, dtype=c64, device=self.dev)
         self.zeta = torch.empty(2 * self.run_samples, ng, dtype=c64, device=self.dev)
         self.source = torch.empty(ns, ng, dtype=f32, device=self.dev)
-        self.uR = torch.empty(ns, N + 1, ng, dtype=f32, device=self.dev)
-        self.u = torch.empty(self.run_samples, N + 1, ng, dtype=c64, device=self.dev)
+        if xi is not None:
+            self.xi = dict(n_xi=int(xi['n_xi']), f_g=float(xi['f_g']), L=int(xi.get('L', 32)),
+                           stream=int(xi.get('stream', stream_id + (1 << 16))))
+            npts = self.xi['n_xi']
+        else:
+            self.xi = None
+            npts = ng
+        self.uR = torch.empty(ns, N + 1, npts, dtype=f32, device=self.dev)
+        self.u = torch.empty(self.run_samples, N + 1, npts, dtype=c64, device=self.dev)
+
+    def _xi_args(self, sample0):
+        x = self.xi
+        return (self.seed, x['stream'], sample0, x['n_xi'], x['f_g'], x['L'])
 
     @contextlib.contextmanager
     def on_stream(self):
@@ -101,16 +120,26 @@ class Pipeline:
 
     def _run_batch(self, sample0, sigma_out, x_out):
         c, ns, ne, N = self.ctx, self.ns, self.n_eta, self.n_steps
+        c.white_noise(self.seed, self.stream_id, sample0, self.run_samples, ne + 1, self.noise)
+        c.filter_occupied(self.coeffs, self.noise, self.filt)
         for g in range(self.group):
             s0 = g * ns
-            c.white_noise(self.seed, self.stream_id, sample0 + s0, ns, ne + 1, self.noise)
-            c.filter_occupied(self.coeffs, self.noise, self.filt)
-            c.prepare_sample(self.noise, self.filt, self.phi, ns, ne, self.eta, self.zeta[2 * s0:2 * (s0 + ns)],
-                             self.source)
+            rows = slice(s0 * (ne + 1), (s0 + ns) * (ne + 1))
+            c.prepare_sample(self.noise[rows], self.filt[rows], self.phi, ns, ne, self.eta,
+                             self.zeta[2 * s0:2 * (s0 + ns)], self.source)
             c.exchange(self.eta, self.phi, ns, ne, x_out[s0:s0 + ns])
-            c.tdh_response(self.eta, self.source, ns, ne, N, self.dt, self.cheb_deg, self.uR)
-            c.time_order(self.uR, self.u[s0:s0 + ns], ns, N)
-        c.sigma_c(self.zeta, self.phi, self.u, self.run_samples, N, self.dt, self.cheb_deg, sigma_out, self.fp64)
+            if self.xi is None:
+                c.tdh_response(self.eta, self.source, ns, ne, N, self.dt, self.cheb_deg, self.uR)
+                c.time_order(self.uR, self.u[s0:s0 + ns], ns, N)
+            else:
+                c.tdh_response_xi(self.eta, self.source, ns, ne, N, self.dt, self.cheb_deg,
+                                  self._xi_args(sample0 + s0), self.uR)
+                c.time_order_points(self.uR, self.u[s0:s0 + ns], ns, N, self.xi['n_xi'])
+        if self.xi is None:
+            c.sigma_c(self.zeta, self.phi, self.u, self.run_samples, N, self.dt, self.cheb_deg, sigma_out, self.fp64)
+        else:
+            c.sigma_c_xi(self.zeta, self.phi, self.u, self.run_samples, N, self.dt, self.cheb_deg,
+                         self._xi_args(sample0), sigma_out, self.fp64)
 
     def run(self, n_samples, sample0=0):
         """Run n_samples (rounded up to whole runs); returns device Sigma [n][2N+1] and X [n]."""

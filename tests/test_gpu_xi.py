@@ -83,3 +83,21 @@ def test_xi_arguments_are_checked():
                 (1, 2, -1, 8, 0.1, 32)):
         with pytest.raises(RuntimeError):
             c.tdh_response_xi(eta, src, 1, 2, 2, 0.05, 16, bad, U)
+
+
+def test_pipeline_xi_sample_indexing():
+    """The TDH chunks (per-chunk sample offsets) and the single Sigma call over the run (run offset)
+    draw the same xi functions: two chunks of one sample equal one chunk of two samples."""
+    build.build()
+    from paper_2601_21005_gb300.pipeline import Pipeline
+    s = synth.wells()
+    g, kb, w, phis = gc.oracle_eigs(s, 8)
+    out = []
+    for ns, group in ((1, 2), (2, 1)):
+        pl = Pipeline(s['n'], s['h'], s['vloc'], [], phis[3], w[3], w[4], n_eta=2, n_steps=6, dt=0.05, cheb_deg=16,
+                      n_cheb=64, samples_per_batch=ns, zeta_group=group, spectrum=(-4.0, 45.0),
+                      xi=dict(n_xi=40, f_g=0.05, L=32))
+        sig, x = pl.run(2, sample0=3)
+        out.append(sig.cpu().numpy())
+        pl.ctx.close()
+    assert gc.rel_err(out[0], out[1]) < 1e-6
