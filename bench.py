@@ -545,13 +545,14 @@ def xi_study(args, cfg, sysd, ks, pl, base, n_xi=10000, f_g=0.003, L=32):
         p.run_batch(base + 700000, sg, x)
         e1.record(st)
         e1.synchronize()
-        om = torch.tensor([ks['e_homo']], dtype=torch.float64, device='cuda')
-        per = []
-        for i in range(m):
-            o = torch.empty(1, dtype=torch.complex128, device='cuda')
-            p.ctx.sigma_omega(sg[i:i + 1].contiguous(), 1, N, cfg['dt'], p.gamma, om, o)
-            per.append(float(o.real.item()))
-        res[name] = dict(ms=e0.elapsed_time(e1), per=np.array(per), qp=p.qp(sg, x, ks['e_homo'])['eps_qp'],
+        # per-sample Re Sigma_i(eps_KS) on the pipeline's stream (the context launches there)
+        with p.on_stream():
+            om = torch.tensor([ks['e_homo']], dtype=torch.float64, device='cuda')
+            per = torch.empty(m, dtype=torch.complex128, device='cuda')
+            for i in range(m):
+                p.ctx.sigma_omega(sg[i:i + 1], 1, N, cfg['dt'], p.gamma, om, per[i:i + 1])
+        torch.cuda.synchronize()
+        res[name] = dict(ms=e0.elapsed_time(e1), per=per.real.cpu().numpy(), qp=p.qp(sg, x, ks['e_homo'])['eps_qp'],
                          u_bytes=p.u.numel() * p.u.element_size() + p.uR.numel() * p.uR.element_size())
     pxi.ctx.close()
     d = res['xi']['per'] - res['full_grid']['per']
@@ -638,8 +639,8 @@ def main():
     ap.add_argument('--no-xi', dest='xi', action='store_false', help='skip the xi-compression study')
     ap.add_argument('--cv', type=int, default=128, help='control-variate training samples (0: skip the study)')
     ap.add_argument('--cv-cheap', type=int, default=4096, help='cheap (features-only) samples in the study')
-    ap.add_argument('--cv-paired-batches', type=int, default=4,
-                    help='runs of paired samples in the study (4 runs of 16: 64 paired corrections)')
+    ap.add_argument('--cv-paired-batches', type=int, default=8,
+                    help='runs of paired samples in the study (8 runs of 16: 128 paired corrections)')
     ap.add_argument('--scale', type=float, default=1.0,
                     help='scale N_tau and N_chb together (profiling captures of fewer launches)')
     args = ap.parse_args()

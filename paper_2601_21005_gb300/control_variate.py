@@ -24,7 +24,9 @@ from . import sgw as _sgw
 
 
 class ControlVariate:
-    def __init__(self, pipeline, m2max=10, width=256, seed=77, max_batch=256, ridge=1e-3):
+    # ridge 0.1 (on standardised inputs): the best held-out variance ratio of the linear part for
+    # 128 and 256 training samples on the 64^3 cluster (2.52 / 2.69 against 2.42 / 2.66 at 1e-3)
+    def __init__(self, pipeline, m2max=10, width=256, seed=77, max_batch=256, ridge=0.1):
         import torch
         self.torch = torch
         self.pl = pipeline
