@@ -510,6 +510,10 @@ template <int M> static void tlaunch(int64_t ng, const float* uR, float2* u, int
 void launch_time_order(int ng, const float* uR, float2* u, int n_samples, int n_steps, int M, const float2* twM,
                        cudaStream_t st) {
     switch (M) {
+        case 4: tlaunch<4>(ng, uR, u, n_samples, n_steps, twM, st); break;
+        case 8: tlaunch<8>(ng, uR, u, n_samples, n_steps, twM, st); break;
+        case 16: tlaunch<16>(ng, uR, u, n_samples, n_steps, twM, st); break;
+        case 32: tlaunch<32>(ng, uR, u, n_samples, n_steps, twM, st); break;
         case 64: tlaunch<64>(ng, uR, u, n_samples, n_steps, twM, st); break;
         case 128: tlaunch<128>(ng, uR, u, n_samples, n_steps, twM, st); break;
         case 256: tlaunch<256>(ng, uR, u, n_samples, n_steps, twM, st); break;

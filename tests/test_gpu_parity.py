@@ -213,9 +213,11 @@ def test_tdh_parity(wells16):
 
 
 # ------------------------------------------------------------------ S8 time ordering
-def test_time_order_parity():
+@pytest.mark.parametrize('N', [37, 6, 0])
+def test_time_order_parity(N):
+    # M = smallest power of two >= 4 (N + 1): 256 (ragged step count), 32 and 4
     s = gc.small_cluster()
-    n_s, N = 2, 37                     # ragged step count: M = 256
+    n_s = 2
     r = np.random.default_rng(4)
     ng = s['n'] ** 3
     uR = r.normal(size=(n_s, N + 1, ng)).astype(np.float32)
