@@ -8,7 +8,11 @@
  * accumulation, and the transform of Sigma to frequency and the QP solve.
  *
  * Conventions (all entry points):
- *  - Grids are cubic, n^3 points with spacing h (bohr); n in {16, 32, 64, 128}.
+ *  - Grids are cubic, n^3 points with spacing h (bohr); n in {16, 32, 64, 128} (plane path: one
+ *    xy plane per CTA, two HBM passes per H application) or n in {48, 96, 288} (row path:
+ *    n = 2^a 3^b, units of 8 x rows per CTA plus y- and z-line passes, four HBM passes per H
+ *    application; the 288^2 plane does not fit one CTA's shared memory).  Results agree between
+ *    the paths to FP32 rounding; the split-operator entries need the plane path (SGW_EINVAL).
  *    A grid function is stored with x fastest: index g = (z*n + y)*n + x.
  *  - A complex vector is interleaved complex64 ("c64": float re, float im), N_g
  *    elements; a batch of B vectors is B contiguous vectors [B][N_g].
@@ -237,7 +241,8 @@ sgw_status sgw_propagate(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, do
  * M_a = R_a E_a R_a^T), atoms grouped into colours of disjoint supports (greedy in atom order),
  * K_asc applying colours 0, 1, .. and K_desc the reverse.  Second order in dt, unitary to
  * rounding, time reversible.  psi_dev [batch][N_g] c64 in place; dir_host as in sgw_propagate.
- * SGW_ESTATE without a potential; graph mode as in sgw_propagate.
+ * SGW_ESTATE without a potential; SGW_EINVAL on a row-path grid (n = 48, 96, 288); graph mode as
+ * in sgw_propagate.
  */
 sgw_status sgw_propagate_split(sgw_ctx* ctx, void* psi_dev, int batch, int n_steps, double dt,
                                const int8_t* dir_host);

@@ -509,7 +509,7 @@ sgw_status sgw_setup_grid(sgw_ctx** out, int nx, int ny, int nz, double h, doubl
     if (!out) return fail(nullptr, SGW_EINVAL, "out is null");
     *out = nullptr;
     if (nx != ny || ny != nz || !sgw::grid_supported(nx))
-        return fail(nullptr, SGW_EINVAL, "grid must be cubic with n in {16,32,64,128}");
+        return fail(nullptr, SGW_EINVAL, "grid must be cubic with n in {16,32,64,128} or {48,96,288}");
     if (!(h > 0) || max_batch < 1) return fail(nullptr, SGW_EINVAL, "h must be > 0 and max_batch >= 1");
     cudaError_t e = cudaSetDevice(device);
     if (e != cudaSuccess) return fail(nullptr, SGW_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
@@ -704,6 +704,8 @@ static sgw_status build_split_tables(sgw_ctx* ctx, int n_atoms, const int* nproj
 static sgw_status split_factors(sgw_ctx* ctx, double dt, const float2** out) {
     const int na = ctx->kb.n_atoms;
     *out = nullptr;
+    if (sgw::rows_path(ctx->n))
+        return fail(ctx, SGW_EINVAL, "the split-operator step is built for power-of-two grids only");
     if (na == 0) return SGW_OK;
     for (auto& t : ctx->split_tabs)
         if (t.first == dt) {
@@ -809,6 +811,7 @@ sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
             const int R = per_sm * nsm;
             cand = {0, R / 2, R, (3 * R) / 2, 2 * R};
         }
+        if (sgw::rows_path(ctx->n)) cand = {ctx->tune[key]};   // the row kernels take no launch hints
         int best_v = 0;
         float best = 1e30f;
         for (int v : cand) {
@@ -870,12 +873,15 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
                 sup_beta[i] = b;
             }
         }
-        // slots: one per (plane, atom) pair where the atom's support meets the plane; atom a's
-        // points in plane z are one contiguous run of its sorted support: [run_beg, run_end)
+        // slots: one per (unit, atom) pair where the atom's support meets the unit (a unit is an xy
+        // plane on the plane path, 8 x rows on the row path: unit_points consecutive points); atom a's
+        // points in unit z are one contiguous run of its sorted support: [run_beg, run_end)
         const int n = ctx->n;
-        const int64_t plane_sz = (int64_t)n * n;
-        std::vector<std::vector<int>> plane_atoms(n);
-        std::vector<std::vector<std::pair<int64_t, int64_t>>> plane_runs(n);
+        const int64_t plane_sz = sgw::unit_points(n);
+        const int nu = (int)(ctx->ng / plane_sz);
+        if (plane_sz > 65536) return fail(ctx, SGW_EINVAL, "in-unit offsets must fit 16 bits");
+        std::vector<std::vector<int>> plane_atoms(nu);
+        std::vector<std::vector<std::pair<int64_t, int64_t>>> plane_runs(nu);
         for (int a = 0; a < n_atoms; ++a) {
             int64_t i = sup_off_host[a];
             while (i < sup_off_host[a + 1]) {
@@ -887,13 +893,13 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
                 i = j;
             }
         }
-        std::vector<int> plane_off(n + 1, 0);
+        std::vector<int> plane_off(nu + 1, 0);
         int max_slots = 0;
-        for (int z = 0; z < n; ++z) {
+        for (int z = 0; z < nu; ++z) {
             plane_off[z + 1] = plane_off[z] + (int)plane_atoms[z].size();
             max_slots = std::max(max_slots, (int)plane_atoms[z].size());
         }
-        const int total_slots = plane_off[n];
+        const int total_slots = plane_off[nu];
         if (max_slots >= 65536) return fail(ctx, SGW_EINVAL, "too many projector supports meet one plane");
         const size_t smem = sgw::plane_step_smem(n, max_slots);
         int optin = 0;
@@ -903,7 +909,7 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
         CK(sgw::plane_step_reserve_smem(n, max_slots));
         std::vector<int> slot_atom(std::max(total_slots, 1));
         std::vector<std::vector<int>> atom_slots(n_atoms);
-        for (int z = 0; z < n; ++z)
+        for (int z = 0; z < nu; ++z)
             for (int k = 0; k < (int)plane_atoms[z].size(); ++k) {
                 slot_atom[plane_off[z] + k] = plane_atoms[z][k];
                 atom_slots[plane_atoms[z][k]].push_back(plane_off[z] + k);
@@ -913,11 +919,11 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
             atom_pos_off[a + 1] = atom_pos_off[a] + (int)atom_slots[a].size();
             atom_pos.insert(atom_pos.end(), atom_slots[a].begin(), atom_slots[a].end());
         }
-        // colour the slots of each plane greedily (lowest colour not used by an overlapping slot)
+        // colour the slots of each unit greedily (lowest colour not used by an overlapping slot)
         std::vector<int> slot_col(std::max(total_slots, 1), 0);
         int max_colors = 0;
         std::vector<uint32_t> mask(plane_sz);
-        for (int z = 0; z < n; ++z) {
+        for (int z = 0; z < nu; ++z) {
             std::fill(mask.begin(), mask.end(), 0u);
             for (int k = 0; k < (int)plane_atoms[z].size(); ++k) {
                 uint32_t used = 0;
@@ -932,14 +938,14 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
                 max_colors = std::max(max_colors, c + 1);
             }
         }
-        // plane-major, colour-major, slot-major entry table
-        std::vector<int> kbe_col((size_t)n * (max_colors + 1), 0);
+        // unit-major, colour-major, slot-major entry table
+        std::vector<int> kbe_col((size_t)nu * (max_colors + 1), 0);
         std::vector<unsigned> kbe_os;
         std::vector<float4> kbe_beta;
         kbe_os.reserve(nsup);
         kbe_beta.reserve(nsup);
         std::vector<int> kbe_slot_beg(std::max(total_slots, 1)), kbe_slot_end(std::max(total_slots, 1));
-        for (int z = 0; z < n; ++z) {
+        for (int z = 0; z < nu; ++z) {
             for (int c = 0; c < max_colors; ++c) {
                 kbe_col[(size_t)z * (max_colors + 1) + c] = (int)kbe_os.size();
                 for (int k = 0; k < (int)plane_atoms[z].size(); ++k) {
@@ -967,7 +973,7 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
                   cudaMalloc(&kb.sup_idx, sizeof(int) * ns1) == cudaSuccess &&
                   cudaMalloc(&kb.sup_beta, sizeof(float4) * ns1) == cudaSuccess &&
                   cudaMalloc(&kb.atom_e, sizeof(float4) * n_atoms) == cudaSuccess &&
-                  cudaMalloc(&kb.plane_off, sizeof(int) * (n + 1)) == cudaSuccess &&
+                  cudaMalloc(&kb.plane_off, sizeof(int) * (nu + 1)) == cudaSuccess &&
                   cudaMalloc(&kb.slot_atom, sizeof(int) * ts1) == cudaSuccess &&
                   cudaMalloc(&kb.kbe_col, sizeof(int) * kbe_col.size()) == cudaSuccess &&
                   cudaMalloc(&kb.kbe_os, sizeof(unsigned) * ns1) == cudaSuccess &&
@@ -988,7 +994,7 @@ sgw_status sgw_set_potential(sgw_ctx* ctx, const float* vloc_dev, int n_atoms, c
         CK(cudaMemcpy(kb.sup_idx, sup_idx_host, sizeof(int) * nsup, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.sup_beta, sup_beta.data(), sizeof(float4) * nsup, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.atom_e, atom_e.data(), sizeof(float4) * n_atoms, cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(kb.plane_off, plane_off.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(kb.plane_off, plane_off.data(), sizeof(int) * (nu + 1), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.slot_atom, slot_atom.data(), sizeof(int) * ts1, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.kbe_col, kbe_col.data(), sizeof(int) * kbe_col.size(), cudaMemcpyHostToDevice));
         CK(cudaMemcpy(kb.kbe_os, kbe_os.data(), sizeof(unsigned) * nsup, cudaMemcpyHostToDevice));
@@ -1524,7 +1530,7 @@ sgw_status sgw_time_order_points(sgw_ctx* ctx, const float* uR_dev, void* u_dev,
     if (n_samples == 0) return SGW_OK;
     if (!uR_dev || !u_dev) return fail(ctx, SGW_EINVAL, "null time-order pointers");
     SGW_ALIGNED(ctx, uR_dev, u_dev);
-    int M = 64;
+    int M = 4;                                    // the smallest power of two >= 4 (n_steps + 1)
     while (M < 4 * (n_steps + 1)) M *= 2;
     if (M > 4096) return fail(ctx, SGW_EINVAL, "n_steps too large for the time-ordering FFT (M <= 4096)");
     if (ctx->twM_n != M) {

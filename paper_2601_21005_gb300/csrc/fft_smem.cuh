@@ -1,7 +1,7 @@
 // Shared-memory FFT building blocks for sm_103a.
 //
 // Batched complex FFTs of lines held in shared memory, by Stockham mixed-radix stages
-// (radix 8, 4 and 2; Govindaraju et al., "High performance discrete Fourier transforms
+// (radix 8, 4, 3 and 2; Govindaraju et al., "High performance discrete Fourier transforms
 // on graphics processors", SC'08).  Each stage reads its butterflies' inputs into
 // registers, synchronises, and writes the outputs back to the same buffer, so the
 // transform runs in place without a ping-pong buffer.
@@ -71,6 +71,20 @@ template <int DIR> struct Dft<8, DIR> {
     }
 };
 
+template <int DIR> struct Dft<3, DIR> {
+    __device__ __forceinline__ static void run(float2* v) {
+        // X_q = sum_r v_r w^(r q), w = exp(dir 2 pi i / 3) = -1/2 + dir i sqrt(3)/2:
+        // X_0 = v0 + s, X_1,2 = v0 - s/2 +- dir i (sqrt(3)/2) d with s = v1 + v2, d = v1 - v2
+        const float h = 0.86602540378443864676f;  // sqrt(3)/2
+        const float2 s = cadd(v[1], v[2]);
+        const float2 d = cscale(mul_i<DIR>(csub(v[1], v[2])), h);
+        const float2 t = make_float2(v[0].x - 0.5f * s.x, v[0].y - 0.5f * s.y);
+        v[0] = cadd(v[0], s);
+        v[1] = cadd(t, d);
+        v[2] = csub(t, d);
+    }
+};
+
 // Twiddle table access: a plain pointer is a global table read through the read-only path;
 // TwShared wraps a copy of the table in shared memory.
 struct TwShared {
@@ -80,9 +94,11 @@ __device__ __forceinline__ float2 tw_at(const float2* __restrict__ t, int i) { r
 __device__ __forceinline__ float2 tw_at(TwShared t, int i) { return t.p[i]; }
 
 // Radix of the next stage given the remaining length: 8 while possible, except that
-// 16 splits as 4 x 4 (fewer registers, same passes).
+// 16 splits as 4 x 4 (fewer registers, same passes); then 4, 2, and 3 for the odd factors.
 template <int REM> struct NextRadix {
-    static constexpr int value = (REM == 16) ? 4 : (REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : 2));
+    static constexpr int value =
+        (REM == 16) ? 4 : (REM % 8 == 0 ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3)));
+    static_assert(REM % value == 0, "lengths must be of the form 2^a 3^b");
 };
 
 // One Stockham stage over NL lines.  Element e of line l is at s[l*LS + e*ES].
@@ -114,7 +130,7 @@ __device__ __forceinline__ void fft_stage(float2* s, TW tw) {
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = tw_at(tw, (r * k * TWS) & (N - 1));
+                    float2 w = tw_at(tw, r * k * TWS);
                     if (DIR > 0) w.y = -w.y;
                     v[p][r] = cmul(v[p][r], w);
                 }
@@ -137,7 +153,8 @@ __device__ __forceinline__ void fft_rec(float2* s, TW tw) {
     }
 }
 
-// NL independent N-point FFTs (N a power of two, 2..4096) in shared memory.
+// NL independent N-point FFTs (N = 2^a 3^b, 2..4096) in shared memory.  Twiddle index
+// r k TWS < N in every stage (r < R, k < NS, TWS = N / (NS R)).
 // Caller must __syncthreads() before (data ready); returns after a barrier.
 template <int N, int NL, int LS, int ES, int NT, int DIR, class TW>
 __device__ __forceinline__ void fft_lines(float2* s, TW tw) {
@@ -168,7 +185,7 @@ __device__ __forceinline__ void stage_r2s(float2 (&v)[PER][R], float2* s, TW tw)
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = tw_at(tw, (r * k * TWS) & (N - 1));
+                    float2 w = tw_at(tw, r * k * TWS);
                     if (DIR > 0) w.y = -w.y;
                     v[p][r] = cmul(v[p][r], w);
                 }
@@ -202,7 +219,7 @@ __device__ __forceinline__ void stage_s2r(const float2* s, float2 (&v)[PER][R], 
             if (NS > 1) {
 #pragma unroll
                 for (int r = 1; r < R; ++r) {
-                    float2 w = tw_at(tw, (r * k * TWS) & (N - 1));
+                    float2 w = tw_at(tw, r * k * TWS);
                     if (DIR > 0) w.y = -w.y;
                     v[p][r] = cmul(v[p][r], w);
                 }

@@ -9,6 +9,7 @@
 // so one Chebyshev term costs two HBM passes over the batch (Sec. 2.2: the cost of each
 // H application is dominated by the FFTs; the potential multiply is fused into them).
 #include "fft_smem.cuh"
+#include "grid_common.cuh"
 #include "sgw_internal.cuh"
 
 namespace sgw {
@@ -32,19 +33,6 @@ template <int N, int NT> struct PlaneMinB {
     static constexpr int v = (N == 64 && NT == 512) ? 3 : 1024 / NT;
     static constexpr int value = N == 128 ? 1 : (v > 6 ? 6 : (v < 1 ? 1 : v));
 };
-
-__device__ __forceinline__ int sfreq(int i, int n) { return i < n / 2 ? i : i - n; }
-
-__device__ __forceinline__ float4 ld4(const float2* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-
-// Bulk prefetch of `bytes` (multiple of 16) at a 16-byte aligned global address into L2; no data
-// reaches the SM, the later loads of the same lines hit L2.
-__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void st4(float2* p, float2 a, float2 b) {
-    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
-}
 
 // ------------------------------------------------------------------ plane <-> smem
 template <int N, int NT>
@@ -81,7 +69,7 @@ constexpr int last_radix(int n) {
     int ns = 1, r = 1;
     while (ns < n) {
         const int rem = n / ns;
-        r = rem == 16 ? 4 : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : 2));
+        r = rem == 16 ? 4 : (rem % 8 == 0 ? 8 : (rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3)));
         ns *= r;
     }
     return r;
@@ -158,20 +146,6 @@ template <> struct ZPlan<16> { static constexpr int R1 = 4, R2 = 4, R3 = 0; };
 template <> struct ZPlan<32> { static constexpr int R1 = 8, R2 = 4, R3 = 0; };
 template <> struct ZPlan<64> { static constexpr int R1 = 8, R2 = 8, R3 = 0; };
 template <> struct ZPlan<128> { static constexpr int R1 = 8, R2 = 4, R3 = 4; };
-
-template <int N, int KIND>
-__device__ __forceinline__ float kspace_factor(int kx, int ky, int kz, float kscale, float ecut) {
-    const int mx = sfreq(kx, N), my = sfreq(ky, N), mz = sfreq(kz, N);
-    const float k2 = kscale * (float)(mx * mx + my * my + mz * mz);
-    float f;
-    if (KIND == 0) {
-        f = 0.5f * k2;
-        if (ecut > 0.f) f = fminf(f, ecut);
-    } else {
-        f = k2 > 0.f ? 12.566370614359172f / k2 : 0.f;   // 4 pi / k^2
-    }
-    return f * (1.0f / ((float)N * N * N));
-}
 
 // Forward z transform of a tile (TX kx-columns at one ky): global -> registers -> ... ->
 // registers holding X[l][kz = j + q NS_last] (butterfly layout of the last stage).
@@ -339,31 +313,6 @@ k_energy_reduce(const double* __restrict__ part, int per, int nblk, double dvn, 
 }
 
 // ------------------------------------------------------------------ fused Chebyshev step
-// Sum 8 per-lane values over a warp by halving exchanges at lane distances 16, 8, 4 (each lane keeps
-// the half selected by its lane bit and adds its partner's copy of that half), then a plain
-// reduction over distances 2 and 1; returns the total of value 4 bit4 + 2 bit3 + bit2 of the lane.
-__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[8], int lane) {
-    float a4[4], a2[2];
-    const bool h4 = (lane >> 4) & 1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float keep = h4 ? v[4 + i] : v[i], give = h4 ? v[i] : v[4 + i];
-        a4[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
-    }
-    const bool h3 = (lane >> 3) & 1;
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float keep = h3 ? a4[2 + i] : a4[i], give = h3 ? a4[i] : a4[2 + i];
-        a2[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
-    }
-    const bool h2 = (lane >> 2) & 1;
-    const float keep = h2 ? a2[1] : a2[0], give = h2 ? a2[0] : a2[1];
-    float t = keep + __shfl_xor_sync(0xffffffffu, give, 4);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
-    return t;
-}
-
 // L2 prefetch of the pointwise operands of plane z of vector b (one thread)
 template <int N>
 __device__ __forceinline__ void prefetch_operands(const StepArgs& a, int z, int b) {
@@ -860,7 +809,7 @@ void launch_kb_reduce(const KBDev& kb, const float2* kbp, int batch, float dV, f
 }
 
 // ------------------------------------------------------------------ launchers
-bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128; }
+bool grid_supported(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || rows_path(n); }
 
 // SMs of the current device (cached per device)
 static int sm_count() {
@@ -875,6 +824,7 @@ static int sm_count() {
 // Dynamic shared memory of the fused plane step: the plane, the twiddle table and 4
 // projections per KB slot
 size_t plane_step_smem(int n, int max_plane_slots) {
+    if (rows_path(n)) return rows_step_smem(n, max_plane_slots);
     return sizeof(float2) * ((size_t)n * (n + 2) + 4 * (size_t)max_plane_slots);
 }
 
@@ -884,7 +834,7 @@ size_t plane_pipe_smem(int n, int max_plane_slots) {
 }
 
 // the persistent form exists up to 64^2 planes (two 128^2 planes do not fit in shared memory)
-bool plane_pipe_supported(int n) { return n <= 64; }
+bool plane_pipe_supported(int n) { return n <= 64 && !rows_path(n); }
 
 template <int N> static cudaError_t set_attrs() {
     cudaError_t e = cudaSuccess;
@@ -924,6 +874,7 @@ template <int N> static cudaError_t set_attrs() {
 }
 
 cudaError_t grid_init_attributes(int n) {
+    if (rows_path(n)) return rows_init_attributes(n);
     switch (n) {
         case 16: return set_attrs<16>();
         case 32: return set_attrs<32>();
@@ -944,6 +895,7 @@ cudaError_t grid_init_attributes(int n) {
 
 // Resident CTAs per SM of the two passes of a Chebyshev term (for the launch-order lookahead)
 cudaError_t plane_step_reserve_smem(int n, int max_plane_slots) {
+    if (rows_path(n)) return rows_step_reserve_smem(n, max_plane_slots);
     cudaError_t e = cudaSuccess;
     const int bytes = (int)plane_step_smem(n, max_plane_slots);
     SGW_DISPATCH_N(n, {
@@ -963,6 +915,7 @@ cudaError_t plane_step_reserve_smem(int n, int max_plane_slots) {
 }
 
 int plane_step_blocks_per_sm(int n, int variant, int max_plane_slots) {
+    if (rows_path(n)) return rows_step_blocks_per_sm(n, max_plane_slots);
     int r = 0;
     const size_t sm = plane_step_smem(n, max_plane_slots);
     if (variant == 2 && !plane_pipe_supported(n)) variant = 0;
@@ -979,6 +932,7 @@ int plane_step_blocks_per_sm(int n, int variant, int max_plane_slots) {
 }
 
 int pencil_blocks_per_sm(int n) {
+    if (rows_path(n)) return zlines_blocks_per_sm(n);
     int r = 0;
     SGW_DISPATCH_N(n, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_pencil<N, 0>, Cfg<N>::PENCIL_NT,
                                                                     Cfg<N>::PENCIL_SMEM));
@@ -986,11 +940,13 @@ int pencil_blocks_per_sm(int n) {
 }
 
 void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st) {
+    if (rows_path(n)) return rows_plane_fwd(n, in, W, batch, tw, st);
     SGW_DISPATCH_N(n, k_plane_fwd<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(in, W, tw));
 }
 
 void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st,
                    int pf_ahead, const VecInfo* info, float dt) {
+    if (rows_path(n)) return rows_pencil(n, W, batch, kind, kscale, ecut, tw, st);
     SGW_DISPATCH_N(n, {
         const dim3 grid((N / Cfg<N>::TX) * N, batch);
         if (kind == 0)
@@ -1006,6 +962,11 @@ int pencil_blocks(int n) { return (n / 16) * n; }
 
 void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
                                   const float2* tw, double* part, double* acc, cudaStream_t st) {
+    if (rows_path(n)) {
+        rows_zlines_energy(n, W, batch, kscale, tw, part, st);
+        if (batch > 0) k_energy_reduce<<<batch / per, 256, 0, st>>>(part, per, pencil_blocks(n), dvn, acc);
+        return;
+    }
     SGW_DISPATCH_N(n, {
         static_assert(Cfg<N>::TX == 16, "pencil_blocks assumes 16-column tiles");
         const dim3 grid((N / Cfg<N>::TX) * N, batch);
@@ -1015,6 +976,7 @@ void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, fl
 }
 
 void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
+    if (rows_path(n)) return rows_plane_step(n, a, batch, tw, st);
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     const size_t sm = plane_step_smem(n, slots);
     if (variant == 2 && !plane_pipe_supported(n)) variant = 0;
@@ -1036,12 +998,14 @@ void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cu
 void launch_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c,
                       const float* vloc, float* vtot, float* dv, float* uR, int64_t uR_stride, float* out_re,
                       cudaStream_t st) {
+    if (rows_path(n)) return rows_plane_inv(n, W, batch, tw, mode, out_c, vloc, vtot, dv, uR, uR_stride, out_re, st);
     SGW_DISPATCH_N(n, k_plane_inv<N><<<dim3(N, batch), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
                               W, tw, mode, out_c, vloc, vtot, dv, uR, uR_stride, out_re));
 }
 
 void launch_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0,
                         int store_rho0, float2* Wp, const float2* tw, cudaStream_t st) {
+    if (rows_path(n)) return rows_density_fwd(n, psi, n_samples, n_eta, weight, rho0, store_rho0, Wp, tw, st);
     SGW_DISPATCH_N(n, k_density_fwd<N><<<dim3(N, n_samples), Cfg<N>::PLANE_NT, Cfg<N>::PLANE_SMEM, st>>>(
                               psi, n_eta, weight, rho0, store_rho0, Wp, tw));
 }

@@ -30,12 +30,13 @@ struct KBDev {
     int* sup_idx = nullptr;      // [n_sup]
     float4* sup_beta = nullptr;  // [n_sup]   beta_a0..3 at each support point
     float4* atom_e = nullptr;    // [n_atoms] E_a0..3
-    // per-plane partial projections: plane z owns slots plane_off[z] .. plane_off[z+1]-1, one per
-    // atom whose support meets the plane (slot_atom[k] is that atom); atom a's slots (in
-    // increasing z) are atom_pos[atom_pos_off[a] .. atom_pos_off[a+1]).
+    // per-unit partial projections (a unit is an xy plane on the plane path, 8 x rows on the row
+    // path): unit z owns slots plane_off[z] .. plane_off[z+1]-1, one per atom whose support meets
+    // the unit (slot_atom[k] is that atom); atom a's slots (in increasing z) are
+    // atom_pos[atom_pos_off[a] .. atom_pos_off[a+1]).
     int total_slots = 0;
     int max_plane_slots = 0;
-    int* plane_off = nullptr;    // [n + 1]
+    int* plane_off = nullptr;    // [units + 1]
     int* slot_atom = nullptr;    // [total_slots]
     // plane-major entries of the fused apply and projections.  The slots of a plane are split into
     // colours whose point sets in the plane are disjoint; plane z's colour c holds the entries
@@ -43,7 +44,7 @@ struct KBDev {
     // (slot k: kbe_slot_beg[k] .. kbe_slot_end[k] - 1).  Entry e: kbe_os[e] = in-plane offset |
     // (plane-local slot << 16), kbe_beta[e] = the slot atom's beta_0..3 at that point.
     int max_colors = 0;
-    int* kbe_col = nullptr;      // [n][max_colors + 1]
+    int* kbe_col = nullptr;      // [units][max_colors + 1]
     unsigned* kbe_os = nullptr;  // [n_sup]
     float4* kbe_beta = nullptr;  // [n_sup]
     int* kbe_slot_beg = nullptr; // [total_slots]
@@ -124,6 +125,27 @@ void launch_kb_reduce(const KBDev& kb, const float2* kbp, int batch, float dV, f
 // density of TDH pairs for each sample, packed as (rho - rho0) + i d rho, fwd xy transformed into Wp.
 void launch_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0,
                         int store_rho0, float2* Wp, const float2* tw, cudaStream_t st);
+
+// ---- row path (kernels_rows.cu): grids of side 2^a 3^b (48, 96, 288) whose planes are split into
+// units of 8 x rows; the launchers above dispatch to it for those sizes.  KB tables, slots and
+// colours are per unit (unit_points(n) consecutive points: n^2 on the plane path, 8 n here).
+bool rows_path(int n);
+int64_t unit_points(int n);
+int rows_units(int n);
+size_t rows_step_smem(int n, int max_unit_slots);
+cudaError_t rows_init_attributes(int n);
+cudaError_t rows_step_reserve_smem(int n, int max_unit_slots);
+int rows_step_blocks_per_sm(int n, int max_unit_slots);
+int zlines_blocks_per_sm(int n);
+void rows_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st);
+void rows_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st);
+void rows_zlines_energy(int n, const float2* W, int batch, float kscale, const float2* tw, double* part,
+                        cudaStream_t st);
+void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st);
+void rows_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c, const float* vloc,
+                    float* vtot, float* dv, float* uR, int64_t uR_stride, float* out_re, cudaStream_t st);
+void rows_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0, int store_rho0,
+                      float2* Wp, const float2* tw, cudaStream_t st);
 
 // ---- other kernels (kernels_misc.cu)
 void launch_noise(int ng, uint64_t seed, uint32_t stream_id, int sample0, int n_samples, int n_vec,
