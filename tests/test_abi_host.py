@@ -73,3 +73,18 @@ def test_control_variate_sizes_match_oracle(lib):
         assert sgw.sgw_cv_shell_count(m2) == omlp.shell_count(m2)
     assert sgw.sgw_cv_linear_size(20, 1603) == 2 * 20 + 1603 + 20 * 1603
     assert sgw.sgw_cv_linear_size(0, 5) == 0
+
+
+@pytest.mark.parametrize('n', [40, 100, 256, 12])
+def test_setup_refuses_unsupported_grid_sides(lib, n):
+    """Grid sides other than 16, 32, 64, 128 (plane path) and 48, 96, 288 (row path) are refused on
+    the host, before any device call, with SGW_EINVAL and a message naming the supported sides."""
+    p = ctypes.c_void_p()
+    st = lib.sgw_setup_grid(ctypes.byref(p), n, n, n, 0.5, 0.0, 1, 0, None)
+    assert st == 1 and not p.value
+    assert b'48,96,288' in lib.sgw_last_error(None)
+
+
+def test_setup_refuses_non_cubic_grids(lib):
+    p = ctypes.c_void_p()
+    assert lib.sgw_setup_grid(ctypes.byref(p), 48, 48, 96, 0.5, 0.0, 1, 0, None) == 1
