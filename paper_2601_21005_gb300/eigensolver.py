@@ -186,7 +186,8 @@ def states_near_gap(ctx, n_occ, emin, emax, m=16, sigma=None, n_probe=16, count_
     """E_HOMO, E_LUMO and the HOMO orbital of an n_occ-occupied system without computing every
     occupied state.  Returns (e_homo, e_lumo, phi_homo [N_g] real float64 normalised to
     dV sum phi^2 = 1, info): info holds the gap centre, the estimated state count there and its
-    standard error, the Ritz values and residuals.  ctx needs max_batch >= max(m, n_probe)."""
+    standard error, the Ritz values and residuals.  When the HOMO level is degenerate, phi_homo is
+    one vector of that level.  ctx needs max_batch >= max(m, n_probe)."""
     import torch
     dev = device if device is not None else torch.device('cuda', ctx.device)
     ctx.set_spectrum(emin, emax)
