@@ -104,6 +104,8 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
  *                               next plane's input into a second shared-memory buffer (cp.async)
  *                               while the current one is transformed (n <= 64; at n = 128 it runs
  *                               as 0)
+ * On row-path grids (n = 48, 96, 288) the keys are accepted and have no effect, and the autotuner
+ * keeps the current values.
  * sgw_set_tuning returns SGW_EINVAL for an unknown key or a negative value (a value above 1 for
  * SGW_TUNE_PLANE_OPERANDS, above 2 for SGW_TUNE_PLANE_VARIANT) and drops the context's cached
  * graphs; sgw_get_tuning writes the current value to *value_host.

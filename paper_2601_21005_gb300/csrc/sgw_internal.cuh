@@ -55,6 +55,7 @@ struct KBDev {
 
 struct StepArgs {
     const float2* W;        // [B][ng] input planes in the xy-transformed / z-filtered representation
+                            // (the row path transforms it back along y in place: W is dead afterwards)
     float2* Wout;           // [B][ng] forward xy transform of the output (nullptr: skip)
     const float2* b1;       // [B][ng] real-space vector H acts on
     const float2* b2;       // [B][ng] real-space b_{k+2} (nullptr when c2 == 0)
@@ -113,7 +114,8 @@ int pencil_blocks(int n);
 void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
                                   const float2* tw, double* part, double* acc, cudaStream_t st);
 void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant = 0);
-// inverse xy transform of W, epilogue: mode 0 -> out_c[b] = plane (c64);
+// inverse xy transform of W (in place along y on the row path; W is scratch), epilogue:
+// mode 0 -> out_c[b] = plane (c64);
 // mode 1 (Poisson of TDH densities) -> vtot[b] = vloc + Re, dv[b] = Im, uR[b] = Im (if uR)
 void launch_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c,
                       const float* vloc, float* vtot, float* dv, float* uR, int64_t uR_stride,
