@@ -9,8 +9,6 @@
 // i.e. four HBM passes per Chebyshev term instead of two (Sec. 2.2: the cost of each H application
 // is dominated by the FFTs; the potential multiply and the KB apply are fused into the row pass).
 // The KB tables are those of the plane path built per unit instead of per plane (see KBDev).
-#include <algorithm>
-
 #include "fft_smem.cuh"
 #include "grid_common.cuh"
 #include "sgw_internal.cuh"

@@ -260,7 +260,8 @@ class MLP:
 
 # ------------------------------------------------------------------ context
 class Context:
-    """Owns one sgw_ctx.  Methods mirror the C entry points (sgw_<name> -> <name>)."""
+    """Owns one sgw_ctx for an n^3 grid (n in 16, 32, 64, 128, or 48, 96, 288 on the row path).
+    Methods mirror the C entry points (sgw_<name> -> <name>)."""
 
     def __init__(self, n, h, ecut=0.0, max_batch=1, device=0, stream=None):
         import torch
