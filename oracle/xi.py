@@ -6,7 +6,7 @@ CPU-baseline leg of the benchmark may use it.
 The paper projects u^R(r, t) on N_xi random functions xi_m supported on short fragmented segments of
 the grid (fraction f_g of the grid each, segments of L points) and carries U_m(t) = <xi_m|u^R(t)>
 instead of u^R on the full grid.  Reading taken here (the construction's details are not given):
-xi_m is the sum of K = round(N_g f_g / L) segment draws; draw k covers the L contiguous flat grid
+xi_m is the sum of K = round(N_g f_g / L) segment draws (nearest integer, halves up); draw k covers the L contiguous flat grid
 points starting at L p_{m,k}, p_{m,k} uniform in [0, N_g / L), with an independent sign per point,
 and the whole function is scaled by c = 1 / sqrt(N_xi K L dV / N_g):
 
@@ -27,7 +27,8 @@ from .philox import philox4x32_10
 
 
 def n_draws(ng, f_g, L):
-    return max(1, int(round(ng * f_g / L)))
+    """K = N_g f_g / L to the nearest integer, halves rounded up, and at least 1."""
+    return max(1, int(np.floor(ng * f_g / L + 0.5)))
 
 
 def draws(seed, stream, sample, n_xi, K, n_seg):

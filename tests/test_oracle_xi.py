@@ -50,3 +50,11 @@ def test_compressed_overlap_is_unbiased():
         vals.append(np.sum(Ua * Uu))
     vals = np.array(vals)
     assert abs(vals.mean() - exact) < 4 * vals.std() / np.sqrt(len(vals))
+
+
+def test_number_of_draws_rounds_halves_up():
+    # N_g f_g / L = 4.5 and 5.5 round to 5 and 6 (not to the even neighbour); at least one draw
+    assert xi.n_draws(4096, 4.5 * 32 / 4096, 32) == 5
+    assert xi.n_draws(4096, 5.5 * 32 / 4096, 32) == 6
+    assert xi.n_draws(4096, 6.4 * 32 / 4096, 32) == 6
+    assert xi.n_draws(4096, 1e-9, 32) == 1
