@@ -6,9 +6,9 @@ CPU-baseline leg of the benchmark may use it.
 The paper projects u^R(r, t) on N_xi random functions xi_m supported on short fragmented segments of
 the grid (fraction f_g of the grid each, segments of L points) and carries U_m(t) = <xi_m|u^R(t)>
 instead of u^R on the full grid.  Reading taken here (the construction's details are not given):
-xi_m is the sum of K = round(N_g f_g / L) segment draws (nearest integer, halves up); draw k covers the L contiguous flat grid
-points starting at L p_{m,k}, p_{m,k} uniform in [0, N_g / L), with an independent sign per point,
-and the whole function is scaled by c = 1 / sqrt(N_xi K L dV / N_g):
+xi_m is the sum of K = round(N_g f_g / L) segment draws (nearest integer, halves up); draw k covers
+the L contiguous flat grid points starting at L p_{m,k}, p_{m,k} uniform in [0, N_g / L), with an
+independent sign per point, and the whole function is scaled by c = 1 / sqrt(N_xi K L dV / N_g):
 
     xi_m(r) = c sum_k [r in segment p_{m,k}] s_{m,k}(r),
 
