@@ -477,11 +477,16 @@ sgw_status sgw_mlp_train_epoch(sgw_mlp* m, const float* x_dev, const float* t_de
  * Same computation and arguments as sgw_qp_energy, without a context: sigma_dev, x_dev and the
  * work run on `stream` (a cudaStream_t, NULL = default) on the current device.  Scratch is a
  * fixed 1 MiB device array inside the library (held on every GPU that loads the library until
- * exit); calls with (2 window/step + 2) + 4 (2 n_steps + 1) + 4 > 131072 doubles are rejected
- * with SGW_EINVAL.  The first call on a device looks up that array's device address, so make it
- * before any stream capture.  All calls on a device share the array: calls that overlap on the
- * GPU (other streams or threads) race and must be serialised by the caller.  Errors are reported
- * through sgw_last_error(NULL).  Synchronises `stream`.
+ * exit).  With n_scan = round(2 window/step) + 1 scan points, a call needs
+ * (n_scan rounded up to even) + 2 (2 n_steps + 1) + 4 doubles; calls that need more than 131072
+ * doubles, or whose 2 window/step is not finite, are rejected with SGW_EINVAL.  Outside a stream
+ * capture every call looks up the array's device address on the current device (so the call
+ * also works after the application resets and re-creates the device's context); during a capture
+ * the address found by an earlier call on that device is used, so make the first call on a
+ * device before any stream capture (otherwise SGW_ESTATE).  All calls on a device share the
+ * array and nothing in it is kept between calls: calls that overlap on the GPU (other streams or
+ * threads) race and must be serialised by the caller.  Errors are reported through
+ * sgw_last_error(NULL).  Synchronises `stream`.
  */
 sgw_status sgw_qp_energy_noalloc(const double* sigma_dev, const double* x_dev, int n_samples,
                                  int n_steps, double dt, double gamma, double eps_ks, double vxc,

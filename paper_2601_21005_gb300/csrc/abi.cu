@@ -1687,7 +1687,9 @@ sgw_status sgw_qp_energy(sgw_ctx* ctx, const double* sigma_dev, const double* x_
     if (s) return s;
     if (n_samples < 1 || n_steps < 0 || !(window > 0) || !(step > 0) || !sigma_dev || !x_dev || !result_host)
         return fail(ctx, SGW_EINVAL, "bad QP arguments");
-    const int n_scan = (int)std::llround(2.0 * window / step) + 1;
+    const double r = 2.0 * window / step;
+    if (!std::isfinite(r) || r + 1.0 > 1e8) return fail(ctx, SGW_EINVAL, "QP scan of 2 window/step + 1 > 1e8 points");
+    const int n_scan = (int)std::llround(r) + 1;
     void* p;
     const size_t bytes = sizeof(double) * (((n_scan + 1) & ~1) + 2 * (2 * n_steps + 1)) + 4 * sizeof(double);
     if ((s = work(ctx, 5, bytes, &p))) return s;

@@ -763,11 +763,19 @@ extern "C" sgw_status sgw_qp_energy_noalloc(const double* sigma_dev, const doubl
         sgw::set_global_error("sgw_qp_energy_noalloc: bad arguments");
         return SGW_EINVAL;
     }
-    const long long n_scan = std::llround(2.0 * window / step) + 1;
+    // the scan size is checked as a double first: a huge window or a tiny step would overflow the
+    // integer conversion
+    const double r = 2.0 * window / step;
+    if (!std::isfinite(r) || r + 1.0 > (double)kQpScratchDoubles) {
+        sgw::set_global_error("sgw_qp_energy_noalloc: 2 window/step + 1 scan points exceed the 1 MiB static scratch "
+                              "(131072 doubles)");
+        return SGW_EINVAL;
+    }
+    const long long n_scan = std::llround(r) + 1;
     const long long need = ((n_scan + 1) & ~1LL) + 2LL * (2LL * n_steps + 1) + 4;
     if (need > kQpScratchDoubles) {
         sgw::set_global_error("sgw_qp_energy_noalloc: window/step and n_steps need more than the 1 MiB static "
-                              "scratch ((2 window/step + 2) + 4 (2 n_steps + 1) + 4 <= 131072 doubles)");
+                              "scratch (even(2 window/step + 1) + 2 (2 n_steps + 1) + 4 <= 131072 doubles)");
         return SGW_EINVAL;
     }
     int dev = 0;
@@ -776,10 +784,19 @@ extern "C" sgw_status sgw_qp_energy_noalloc(const double* sigma_dev, const doubl
         sgw::set_global_error("sgw_qp_energy_noalloc: no usable current device");
         return SGW_ECUDA;
     }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) {
+        sgw::set_global_error((std::string("sgw_qp_energy_noalloc: ") + cudaGetErrorString(e)).c_str());
+        return SGW_ECUDA;
+    }
     double* scratch = nullptr;
     {
+        // Outside a capture the address is looked up on every call (cheap), so a context that the
+        // application reset and re-created gets the new one; during a capture the address cached
+        // by an earlier call on this device is used.
         std::lock_guard<std::mutex> lk(g_qp_scratch_mu);
-        if (!g_qp_scratch_dev[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_qp_scratch);
             if (e != cudaSuccess || !p) {
@@ -788,10 +805,13 @@ extern "C" sgw_status sgw_qp_energy_noalloc(const double* sigma_dev, const doubl
                 return SGW_ECUDA;
             }
             g_qp_scratch_dev[dev] = static_cast<double*>(p);
+        } else if (!g_qp_scratch_dev[dev]) {
+            sgw::set_global_error("sgw_qp_energy_noalloc: the first call on a device must come before any stream "
+                                  "capture");
+            return SGW_ESTATE;
         }
         scratch = g_qp_scratch_dev[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
     // scan values, then the damped terms, then the 4 result doubles; every element read in
     // this call is written first in this call, so nothing needs clearing between calls.
     double* result = scratch + (need - 4);

@@ -38,7 +38,20 @@ def test_noalloc_qp_matches_context_qp_twice():
         got = sgw.sgw_qp_energy_noalloc(sd, xd, n_s, N, dt, gamma, -0.25)
         for k in ('eps_qp', 'se', 're_sigma', 'z'):
             assert abs(got[k] - ref[k]) <= 1e-10 * max(1.0, abs(ref[k])), (call, k)
-    # sizes beyond the static scratch are rejected with a clear error
-    with pytest.raises(sgw.SgwError) as ei:
-        sgw.sgw_qp_energy_noalloc(sd, xd, n_s, N, dt, gamma, -0.25, window=200.0, step=1e-3)
-    assert 'static' in str(ei.value)
+    # the largest request that fits: n_scan = 2 w/s + 1 = 130265 (130266 rounded to even) +
+    # 2 (2 N + 1) + 4 = 131072 doubles, exactly the scratch size
+    w_max = 65.132
+    ref = ctx.qp_energy(sd, xd, n_s, N, dt, gamma, -0.25, window=w_max)
+    got = sgw.sgw_qp_energy_noalloc(sd, xd, n_s, N, dt, gamma, -0.25, window=w_max)
+    for k in ('eps_qp', 'se', 're_sigma', 'z'):
+        assert abs(got[k] - ref[k]) <= 1e-10 * max(1.0, abs(ref[k])), k
+    # sizes beyond the static scratch are rejected with a clear error, before any launch: one
+    # scan point too many, a large window, and a window/step ratio that overflows any integer
+    for window, step in ((65.133, 1e-3), (200.0, 1e-3), (1e300, 1e-300)):
+        with pytest.raises(sgw.SgwError) as ei:
+            sgw.sgw_qp_energy_noalloc(sd, xd, n_s, N, dt, gamma, -0.25, window=window, step=step)
+        assert 'static' in str(ei.value), (window, step)
+    # the array is still usable afterwards
+    got = sgw.sgw_qp_energy_noalloc(sd, xd, n_s, N, dt, gamma, -0.25)
+    ref = ctx.qp_energy(sd, xd, n_s, N, dt, gamma, -0.25)
+    assert abs(got['eps_qp'] - ref['eps_qp']) <= 1e-10 * max(1.0, abs(ref['eps_qp']))
