@@ -107,9 +107,12 @@ def step_coeffs(e, emin, emax, degree):
     return out[0] if np.ndim(e) == 0 else out
 
 
-def gaussian_coeffs(center, sigma, emin, emax, degree):
+def gaussian_coeffs(center, sigma, emin, emax, degree, damped=False):
     """Chebyshev coefficients of exp(-(H - center)^2 / (2 sigma^2)) on [emin, emax] by Chebyshev-Gauss
-    quadrature at 4 (degree + 1) nodes (discrete orthogonality of the T_k there)."""
+    quadrature at 4 (degree + 1) nodes (discrete orthogonality of the T_k there).  damped=True
+    multiplies them by the Jackson factors: the truncated series then has no Gibbs oscillations
+    (it stays positive and small far from the centre) at the price of a width broadened by about
+    pi (emax - emin) / (2 degree)."""
     M = 4 * (degree + 1)
     th = np.pi * (np.arange(M) + 0.5) / M
     c, h = 0.5 * (emax + emin), 0.5 * (emax - emin)
@@ -117,7 +120,7 @@ def gaussian_coeffs(center, sigma, emin, emax, degree):
     k = np.arange(degree + 1)
     out = (2.0 / M) * (np.cos(np.outer(k, th)) @ f)
     out[0] *= 0.5
-    return out
+    return out * jackson_kernel(degree) if damped else out
 
 
 def cheb_moments(ctx, emin, emax, n_probe=16, degree=1000, seed=777, device=None):
@@ -182,19 +185,28 @@ def find_gap(mu, n_occ, emin, emax, n_grid=4000):
 
 
 def states_near_gap(ctx, n_occ, emin, emax, m=16, sigma=None, n_probe=16, count_degree=1000,
-                    window_degree=400, max_iter=60, tol=1e-5, seed=4243, device=None):
+                    window_degree=2000, max_iter=60, tol=2e-4, seed=4243, device=None, log=None):
     """E_HOMO, E_LUMO and the HOMO orbital of an n_occ-occupied system without computing every
     occupied state.  Returns (e_homo, e_lumo, phi_homo [N_g] real float64 normalised to
     dV sum phi^2 = 1, info): info holds the gap centre, the estimated state count there and its
     standard error, the Ritz values and residuals.  When the HOMO level is degenerate, phi_homo is
-    one vector of that level.  ctx needs max_batch >= max(m, n_probe)."""
+    one vector of that level.  ctx needs max_batch >= max(m, n_probe).  log: optional callable
+    taking a progress line (the gap search, then each iteration's HOMO/LUMO Ritz values).
+
+    The window is the Jackson-damped Gaussian of degree window_degree; its default width sigma is
+    1.5 pi (emax - emin) / (2 window_degree), the smallest the damped series resolves, so that the
+    states next to the gap are amplified most against their neighbours.  tol is the relative
+    residual at which the HOMO and LUMO Ritz pairs count as converged; FP32 H applications floor
+    the residual near 1e-4 of |H|, hence the default 2e-4."""
     import torch
     dev = device if device is not None else torch.device('cuda', ctx.device)
     ctx.set_spectrum(emin, emax)
     mu = cheb_moments(ctx, emin, emax, n_probe, count_degree, device=dev)
     ef, n_ef, se_ef = find_gap(mu, n_occ, emin, emax)
-    sig = sigma if sigma is not None else 0.01 * (emax - emin)
-    coeff = gaussian_coeffs(ef, sig, emin, emax, window_degree)
+    if log:
+        log('gap search: centre %.6f Ha, estimated count %.1f +- %.1f (n_occ %d)' % (ef, n_ef, se_ef, n_occ))
+    sig = sigma if sigma is not None else 1.5 * np.pi * 0.5 * (emax - emin) / window_degree
+    coeff = gaussian_coeffs(ef, sig, emin, emax, window_degree, damped=True)
     X = torch.empty(m, ctx.ng, dtype=torch.complex64, device=dev)
     ctx.white_noise(seed, 0xE16F, 0, 1, m, X)
     Y = torch.empty_like(X)
@@ -227,8 +239,10 @@ def states_near_gap(ctx, n_occ, emin, emax, m=16, sigma=None, n_probe=16, count_
 
     Q = orth(X)
     w, Q, res = rayleigh_ritz(Q)
-    for _ in range(max_iter):
+    for it in range(max_iter):
         ih, il = pair(w)
+        if log and ih is not None and il is not None:
+            log('iteration %d: HOMO %.8f (res %.1e), LUMO %.8f (res %.1e)' % (it, w[ih], res[ih], w[il], res[il]))
         if ih is not None and il is not None and max(res[ih], res[il]) < tol * max(1.0, abs(w[ih]), abs(w[il])):
             break
         ctx.filter_occupied(coeff, Q, X)

@@ -30,6 +30,9 @@ def main():
     ap.add_argument('--f-g', type=float, default=0.003)
     ap.add_argument('--n-cheb', type=int, default=2000)
     ap.add_argument('--ks', action='store_true', help='KS inputs from the interior eigensolver')
+    ap.add_argument('--gap-only', action='store_true',
+                    help='only the kernel-polynomial gap search (state count and density of states near n_occ)')
+    ap.add_argument('--ks-max-iter', type=int, default=60)
     args = ap.parse_args()
     build.build()
     n, h = 288, 0.5
@@ -38,6 +41,22 @@ def main():
     t_sys = time.perf_counter() - t0
     c = 0.5 * n * h
     ks = None
+    if args.gap_only:
+        from . import sgw
+        from .eigensolver import cheb_moments, count_and_dos, find_gap
+        t1 = time.perf_counter()
+        kctx = sgw.Context(n, h, max_batch=16)
+        kctx.set_potential(torch.as_tensor(s['vloc'].reshape(-1).astype(np.float32)).cuda(), s['kb_atoms'])
+        (emin, emax), _ = kctx.spectral_bounds(200, 1000, 0.05)
+        mu = cheb_moments(kctx, emin, emax, 16, 2000)
+        ef, n_ef, se_ef = find_gap(mu, s['n_occ'], emin, emax)
+        e = np.linspace(ef - 0.3, ef + 0.3, 61)
+        cnt, se, dos = count_and_dos(mu, e, emin, emax)
+        kctx.close()
+        print(json.dumps(dict(workload=s['name'], n_occ=s['n_occ'], spectrum=[emin, emax], gap_centre=ef,
+                              count_at_gap=n_ef, count_se=se_ef, seconds=round(time.perf_counter() - t1, 1),
+                              scan=dict(e=e.round(4).tolist(), count=cnt.round(1).tolist(), dos=dos.round(1).tolist()))))
+        return
     if args.ks:
         from . import sgw
         from .eigensolver import states_near_gap
@@ -46,7 +65,8 @@ def main():
         kctx.set_potential(torch.as_tensor(s['vloc'].reshape(-1).astype(np.float32)).cuda(), s['kb_atoms'])
         (emin, emax), _ = kctx.spectral_bounds(200, 1000, 0.05)
         e_homo, e_lumo, phi, info = states_near_gap(kctx, s['n_occ'], emin, emax, m=32, sigma=0.05, n_probe=16,
-                                                    count_degree=2000, window_degree=1500)
+                                                    count_degree=2000, window_degree=1500,
+                                                    max_iter=args.ks_max_iter, log=lambda m: print(m, flush=True))
         kctx.close()
         ks = dict(e_homo=e_homo, e_lumo=e_lumo, gap_eV=(e_lumo - e_homo) * 27.211386245988,
                   gap_centre=info['gap_centre'], count_at_gap=info['count_at_gap'], count_se=info['count_se'],

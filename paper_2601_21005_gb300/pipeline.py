@@ -118,10 +118,29 @@ class Pipeline:
         with self.on_stream():
             self._run_batch(sample0, sigma_out, x_out)
 
-    def _run_batch(self, sample0, sigma_out, x_out):
-        c, ns, ne, N = self.ctx, self.ns, self.n_eta, self.n_steps
+    def filter_batch(self, sample0):
+        """White noise and the occupied filter (Eq. 3) of samples sample0 .. sample0 + run_samples - 1,
+        kept in the pipeline for `propagate_batch`."""
+        with self.on_stream():
+            self._filter_batch(sample0)
+
+    def propagate_batch(self, sample0, sigma_out, x_out):
+        """Everything after the filter for the batch `filter_batch` left (sample0 must be the same):
+        exchange, TDH, time ordering, zeta propagation and Sigma(t)."""
+        with self.on_stream():
+            self._propagate_batch(sample0, sigma_out, x_out)
+
+    def _filter_batch(self, sample0):
+        c, ne = self.ctx, self.n_eta
         c.white_noise(self.seed, self.stream_id, sample0, self.run_samples, ne + 1, self.noise)
         c.filter_occupied(self.coeffs, self.noise, self.filt)
+
+    def _run_batch(self, sample0, sigma_out, x_out):
+        self._filter_batch(sample0)
+        self._propagate_batch(sample0, sigma_out, x_out)
+
+    def _propagate_batch(self, sample0, sigma_out, x_out):
+        c, ns, ne, N = self.ctx, self.ns, self.n_eta, self.n_steps
         for g in range(self.group):
             s0 = g * ns
             rows = slice(s0 * (ne + 1), (s0 + ns) * (ne + 1))
