@@ -72,7 +72,7 @@ struct sgw_ctx {
     // one device table per dt used so far (graphs keep pointing at the table of their dt)
     std::vector<std::pair<double, float2*>> split_tabs;
     // launch tuning hints (sgw_set_tuning / sgw_autotune); no result depends on them
-    int tune[SGW_TUNE_KEYS] = {1, 0, 0, 0};
+    int tune[SGW_TUNE_KEYS] = {1, 0, 0, 0, 0};
     std::string err;
 };
 
@@ -366,7 +366,7 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
         {
             Launch L(ctx, SGW_PROF_PENCIL, 1, 16.0 * (double)ctx->ng * batch);
             sgw::launch_pencil(n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, st,
-                               ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD]);
+                               ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD], nullptr, 0.f, ctx->tune[SGW_TUNE_LINE_FORM]);
             CKL();
         }
         sgw::StepArgs a{};
@@ -742,7 +742,8 @@ static sgw_status split_factors(sgw_ctx* ctx, double dt, const float2** out) {
 sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value) {
     if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
     if (key < 0 || key >= SGW_TUNE_KEYS) return fail(ctx, SGW_EINVAL, "unknown tuning key");
-    if (value < 0 || (key == SGW_TUNE_PLANE_OPERANDS && value > 1) || (key == SGW_TUNE_PLANE_VARIANT && value > 2))
+    if (value < 0 || (key == SGW_TUNE_PLANE_OPERANDS && value > 1) || (key == SGW_TUNE_PLANE_VARIANT && value > 2) ||
+        (key == SGW_TUNE_LINE_FORM && value > 2))
         return fail(ctx, SGW_EINVAL, "tuning value out of range");
     clear_graphs(ctx);
     ctx->tune[key] = value;
@@ -799,7 +800,7 @@ sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
         return SGW_OK;
     };
     const int order[SGW_TUNE_KEYS] = {SGW_TUNE_PLANE_VARIANT, SGW_TUNE_PLANE_OPERANDS, SGW_TUNE_PLANE_LOOKAHEAD,
-                                      SGW_TUNE_PENCIL_LOOKAHEAD};
+                                      SGW_TUNE_PENCIL_LOOKAHEAD, SGW_TUNE_LINE_FORM};
     for (int ki = 0; ki < SGW_TUNE_KEYS && !s; ++ki) {
         const int key = order[ki];
         std::vector<int> cand = {0, 1};
@@ -811,7 +812,10 @@ sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
             const int R = per_sm * nsm;
             cand = {0, R / 2, R, (3 * R) / 2, 2 * R};
         }
-        if (sgw::rows_path(ctx->n)) cand = {ctx->tune[key]};   // the row kernels take no launch hints
+        if (key == SGW_TUNE_LINE_FORM) cand = sgw::cluster_plane(ctx->n) ? std::vector<int>{0, 1, 2}
+                                                                          : std::vector<int>{ctx->tune[key]};
+        else if (key == SGW_TUNE_PLANE_VARIANT && sgw::cluster_plane(ctx->n)) cand = {0, 1, 2};
+        else if (sgw::rows_path(ctx->n)) cand = {ctx->tune[key]};   // the row kernels take no other launch hints
         int best_v = 0;
         float best = 1e30f;
         for (int v : cand) {
@@ -1035,7 +1039,7 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     {
         Launch L(ctx, SGW_PROF_PENCIL);
         sgw::launch_pencil(ctx->n, ctx->W, batch, 0, kscale, (float)ctx->ecut, ctx->tw, ctx->stream,
-                           ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD]);
+                           ctx->tune[SGW_TUNE_PENCIL_LOOKAHEAD], nullptr, 0.f, ctx->tune[SGW_TUNE_LINE_FORM]);
         CKL();
     }
     sgw::StepArgs a{};
@@ -1462,7 +1466,8 @@ static sgw_status tdh_run(sgw_ctx* ctx, const void* eta_dev, const float* source
             Launch L(ctx, SGW_PROF_OTHER, 5);
             sgw::launch_real_to_c64(ng * n_samples, source_dev, ctx->B1, st);
             sgw::launch_plane_fwd(n, ctx->B1, Wp, n_samples, ctx->tw, st);
-            sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+            sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st, 0, nullptr, 0.f,
+                               ctx->tune[SGW_TUNE_LINE_FORM]);
             sgw::launch_plane_inv(n, Wp, n_samples, ctx->tw, 2, nullptr, nullptr, nullptr, nullptr, nullptr, 0, vp, st);
             // eta pairs: (eta, d eta = -i v_p eta)
             sgw::launch_kick((int)ng, (const float2*)eta_dev, vp, n_samples, n_eta, psi, st);
@@ -1476,7 +1481,8 @@ static sgw_status tdh_run(sgw_ctx* ctx, const void* eta_dev, const float* source
             }
             {
                 Launch L(ctx, SGW_PROF_OTHER);
-                sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st);
+                sgw::launch_pencil(n, Wp, n_samples, 1, kscale, 0.f, ctx->tw, st, 0, nullptr, 0.f,
+                               ctx->tune[SGW_TUNE_LINE_FORM]);
             }
             {
                 Launch L(ctx, SGW_PROF_OTHER);

@@ -153,6 +153,16 @@ __device__ __forceinline__ void fft_rec(float2* s, TW tw) {
     }
 }
 
+// Stages with sub-length NS in [NS, NSTOP)
+template <int N, int NS, int NSTOP, int NL, int LS, int ES, int NT, int DIR, class TW>
+__device__ __forceinline__ void fft_rec_until(float2* s, TW tw) {
+    if constexpr (NS < NSTOP) {
+        constexpr int R = NextRadix<N / NS>::value;
+        fft_stage<N, R, NS, NL, LS, ES, NT, DIR>(s, tw);
+        fft_rec_until<N, NS * R, NSTOP, NL, LS, ES, NT, DIR, TW>(s, tw);
+    }
+}
+
 // NL independent N-point FFTs (N = 2^a 3^b, 2..4096) in shared memory.  Twiddle index
 // r k TWS < N in every stage (r < R, k < NS, TWS = N / (NS R)).
 // Caller must __syncthreads() before (data ready); returns after a barrier.

@@ -75,16 +75,6 @@ constexpr int last_radix(int n) {
     return r;
 }
 
-// Stages with sub-length NS in [NS, NSTOP)
-template <int N, int NS, int NSTOP, int NL, int LS, int ES, int NT, int DIR, class TW>
-__device__ __forceinline__ void fft_rec_until(float2* s, TW tw) {
-    if constexpr (NS < NSTOP) {
-        constexpr int R = NextRadix<N / NS>::value;
-        fft_stage<N, R, NS, NL, LS, ES, NT, DIR>(s, tw);
-        fft_rec_until<N, NS * R, NSTOP, NL, LS, ES, NT, DIR, TW>(s, tw);
-    }
-}
-
 // Inverse xy transform of a plane read from global memory: the first stage along y takes its
 // inputs straight from global (consecutive threads on consecutive x: coalesced rows), the
 // remaining stages run in shared memory; the result is left in sm (pitch N + 1).
@@ -915,7 +905,7 @@ cudaError_t plane_step_reserve_smem(int n, int max_plane_slots) {
 }
 
 int plane_step_blocks_per_sm(int n, int variant, int max_plane_slots) {
-    if (rows_path(n)) return rows_step_blocks_per_sm(n, max_plane_slots);
+    if (rows_path(n)) return rows_step_blocks_per_sm(n, variant, max_plane_slots);
     int r = 0;
     const size_t sm = plane_step_smem(n, max_plane_slots);
     if (variant == 2 && !plane_pipe_supported(n)) variant = 0;
@@ -945,8 +935,8 @@ void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float
 }
 
 void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st,
-                   int pf_ahead, const VecInfo* info, float dt) {
-    if (rows_path(n)) return rows_pencil(n, W, batch, kind, kscale, ecut, tw, st);
+                   int pf_ahead, const VecInfo* info, float dt, int line_form) {
+    if (rows_path(n)) return rows_pencil(n, W, batch, kind, kscale, ecut, tw, st, line_form);
     SGW_DISPATCH_N(n, {
         const dim3 grid((N / Cfg<N>::TX) * N, batch);
         if (kind == 0)
@@ -976,7 +966,7 @@ void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, fl
 }
 
 void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
-    if (rows_path(n)) return rows_plane_step(n, a, batch, tw, st);
+    if (rows_path(n)) return rows_plane_step(n, a, batch, tw, st, variant);
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     const size_t sm = plane_step_smem(n, slots);
     if (variant == 2 && !plane_pipe_supported(n)) variant = 0;

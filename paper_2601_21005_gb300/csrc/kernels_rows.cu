@@ -11,6 +11,7 @@
 // The KB tables are those of the plane path built per unit instead of per plane (see KBDev).
 #include "fft_smem.cuh"
 #include "grid_common.cuh"
+#include "kb_unit.cuh"
 #include "sgw_internal.cuh"
 
 namespace sgw {
@@ -20,7 +21,12 @@ constexpr int RNT = 256;   // threads of the row and line kernels
 constexpr int LT = 16;     // x columns per y- or z-line tile (16 x 8 B = 128 B rows)
 
 bool rows_path(int n) { return n == 48 || n == 96 || n == 288; }
-int64_t unit_points(int n) { return rows_path(n) ? (int64_t)RR * n : (int64_t)n * n; }
+// KB unit: an xy plane on the plane path, RR x rows on the row path, a CTA's rows of a plane when a
+// cluster of CTAs holds the plane (288)
+int64_t unit_points(int n) {
+    if (cluster_plane(n)) return (int64_t)cluster_unit_rows() * n;
+    return rows_path(n) ? (int64_t)RR * n : (int64_t)n * n;
+}
 
 // ------------------------------------------------------------------ units of rows <-> smem
 // A unit is RR consecutive x rows (RR N points, contiguous in memory); in shared memory row y of
@@ -244,93 +250,16 @@ __global__ void __launch_bounds__(RNT) k_rows_step(StepArgs a, const float2* __r
     const size_t uoff = (size_t)u * RR * N;
     const size_t off = (size_t)b * NG + uoff;
     const VecInfo inf = a.info[b];
-    const float* V = a.vpot + (size_t)inf.vrow * NG + uoff;
-    const float* dV = (a.dvpot != nullptr && inf.dvrow >= 0) ? a.dvpot + (size_t)inf.dvrow * NG + uoff : nullptr;
-    const float2* bp = (dV != nullptr) ? a.b1 + (size_t)inf.partner * NG + uoff : nullptr;
     const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
-    if (kc != nullptr) {
-        const int s0 = __ldg(a.plane_off + u), ns = __ldg(a.plane_off + u + 1) - s0;
-        for (int i = threadIdx.x; i < 4 * ns; i += RNT) kcs[i] = kc[__ldg(a.slot_atom + s0 + i / 4) * 4 + (i & 3)];
-    }
+    if (kc != nullptr) kb_stage_coeffs<RNT>(a, kc, u, kcs);
     load_rows<N>(sm, a.W + off);
     __syncthreads();
     fft_lines<N, RR, P, 1, RNT, +1>(sm, tws);
-    if (kc != nullptr) {
-        const int* col = a.kbe_col + (size_t)u * (a.max_colors + 1);
-        for (int c = 0; c < a.max_colors; ++c) {
-            const int e0 = __ldg(col + c), e1 = __ldg(col + c + 1);
-            if (e0 == e1) break;                  // a unit's colours are used from 0 upwards
-            for (int e = e0 + threadIdx.x; e < e1; e += RNT) {
-                const unsigned os = __ldg(a.kbe_os + e);
-                const float4 be = __ldg(a.kbe_beta + e);
-                const int o = (int)(os & 0xffffu), sl = (int)(os >> 16);
-                const float4 c01 = *reinterpret_cast<const float4*>(kcs + 4 * sl);
-                const float4 c23 = *reinterpret_cast<const float4*>(kcs + 4 * sl + 2);
-                float2& hv = sm[(o / N) * P + (o % N)];
-                hv.x += be.x * c01.x + be.y * c01.z + be.z * c23.x + be.w * c23.z;
-                hv.y += be.x * c01.y + be.y * c01.w + be.z * c23.y + be.w * c23.w;
-            }
-            __syncthreads();
-        }
-    }
-    const float2 cpsi = a.coef.cpsi[inf.cset], ch = a.coef.ch[inf.cset], c2 = a.coef.c2[inf.cset];
-    const float ebar = a.ebar, alpha = a.alpha;
-    for (int q = threadIdx.x; q < RR * N / 2; q += RNT) {
-        const int y = q / (N / 2), x = 2 * (q % (N / 2));
-        const int o = y * N + x;
-        float2 h0 = sm[y * P + x], h1 = sm[y * P + x + 1];
-        const float4 bb = ld4(a.b1 + off + o);
-        const float2 v = __ldg(reinterpret_cast<const float2*>(V + o));
-        h0.x += (v.x - ebar) * bb.x;
-        h0.y += (v.x - ebar) * bb.y;
-        h1.x += (v.y - ebar) * bb.z;
-        h1.y += (v.y - ebar) * bb.w;
-        if (dV != nullptr) {
-            const float2 d = __ldg(reinterpret_cast<const float2*>(dV + o));
-            const float4 pb = ld4(bp + o);
-            h0.x += d.x * pb.x;
-            h0.y += d.x * pb.y;
-            h1.x += d.y * pb.z;
-            h1.y += d.y * pb.w;
-        }
-        float2 o0 = cmul(ch, cscale(h0, alpha)), o1 = cmul(ch, cscale(h1, alpha));
-        if (a.psi != nullptr) {
-            const float4 pp = ld4(a.psi + off + o);
-            o0 = cadd(o0, cmul(cpsi, make_float2(pp.x, pp.y)));
-            o1 = cadd(o1, cmul(cpsi, make_float2(pp.z, pp.w)));
-        }
-        if (a.b2 != nullptr) {
-            const float4 b2 = ld4(a.b2 + off + o);
-            o0 = cadd(o0, cmul(c2, make_float2(b2.x, b2.y)));
-            o1 = cadd(o1, cmul(c2, make_float2(b2.z, b2.w)));
-        }
-        st4(a.out + off + o, o0, o1);
-        sm[y * P + x] = o0;
-        sm[y * P + x + 1] = o1;
-    }
+    if (kc != nullptr) kb_apply_unit<N, P, RNT>(a, u, kcs, sm);
+    step_pointwise<N, RR, P, RNT>(a, inf, off, uoff, sm);
     if (a.Wout == nullptr) return;
     __syncthreads();
-    if (a.kbp != nullptr) {
-        // partial projections of `out` on this unit: one warp per (unit, atom) slot, fixed order
-        const int sb = __ldg(a.plane_off + u), s1 = __ldg(a.plane_off + u + 1);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int k = sb + warp; k < s1; k += RNT / 32) {
-            float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const int e1 = __ldg(a.kbe_slot_end + k);
-            for (int e = __ldg(a.kbe_slot_beg + k) + lane; e < e1; e += 32) {
-                const int o = (int)(__ldg(a.kbe_os + e) & 0xffffu);
-                const float2 v = sm[(o / N) * P + (o % N)];
-                const float4 be = __ldg(a.kbe_beta + e);
-                acc[0] += be.x * v.x; acc[1] += be.x * v.y;
-                acc[2] += be.y * v.x; acc[3] += be.y * v.y;
-                acc[4] += be.z * v.x; acc[5] += be.z * v.y;
-                acc[6] += be.w * v.x; acc[7] += be.w * v.y;
-            }
-            const float r = warp_reduce_scatter8(acc, lane);
-            if ((lane & 3) == 0)
-                reinterpret_cast<float*>(a.kbp + ((size_t)b * a.total_slots + k) * 4)[lane >> 2] = r;
-        }
-    }
+    if (a.kbp != nullptr) kb_project_unit<N, P, RNT>(a, u, b, sm);
     fft_lines<N, RR, P, 1, RNT, -1>(sm, tws);
     store_rows<N>(a.Wout + off, sm);
 }
@@ -346,7 +275,10 @@ __global__ void __launch_bounds__(RNT) k_rows_step(StepArgs a, const float2* __r
 
 static size_t rows_smem(int n) { return sizeof(float2) * ((size_t)RR * (n + 1) + n); }
 static size_t lines_smem(int n) { return sizeof(float2) * ((size_t)n * LT + n); }
-size_t rows_step_smem(int n, int max_unit_slots) { return rows_smem(n) + sizeof(float2) * 4 * (size_t)max_unit_slots; }
+size_t rows_step_smem(int n, int max_unit_slots) {
+    if (cluster_plane(n)) return cplane_smem(max_unit_slots);
+    return rows_smem(n) + sizeof(float2) * 4 * (size_t)max_unit_slots;
+}
 int rows_units(int n) { return n * n / RR; }
 
 template <int N> static cudaError_t rows_attrs(int slots) {
@@ -371,17 +303,20 @@ template <int N> static cudaError_t rows_attrs(int slots) {
 cudaError_t rows_init_attributes(int n) {
     cudaError_t e = cudaErrorInvalidValue;
     SGW_DISPATCH_ROWS(n, e = rows_attrs<N>(0));
+    if (e == cudaSuccess && cluster_plane(n)) e = cluster_init_attributes(0);
     return e;
 }
 
 cudaError_t rows_step_reserve_smem(int n, int max_unit_slots) {
+    if (cluster_plane(n)) return cluster_init_attributes(max_unit_slots);
     cudaError_t e = cudaErrorInvalidValue;
     SGW_DISPATCH_ROWS(n, e = cudaFuncSetAttribute(k_rows_step<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                   (int)rows_step_smem(N, max_unit_slots)));
     return e;
 }
 
-int rows_step_blocks_per_sm(int n, int max_unit_slots) {
+int rows_step_blocks_per_sm(int n, int variant, int max_unit_slots) {
+    if (cluster_plane(n)) return cplane_blocks_per_sm(variant, max_unit_slots);
     int r = 0;
     SGW_DISPATCH_ROWS(n, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_rows_step<N>, RNT,
                                                                        rows_step_smem(N, max_unit_slots)));
@@ -389,6 +324,7 @@ int rows_step_blocks_per_sm(int n, int max_unit_slots) {
 }
 
 int zlines_blocks_per_sm(int n) {
+    if (cluster_plane(n)) return zlines_reg_blocks_per_sm(0);
     int r = 0;
     SGW_DISPATCH_ROWS(n, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_zlines<N, 0>, RNT, lines_smem(N)));
     return r;
@@ -410,8 +346,10 @@ void rows_plane_fwd(int n, const float2* in, float2* W, int batch, const float2*
     ylines(n, W, batch, -1, tw, st);
 }
 
-void rows_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st) {
+void rows_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st,
+                 int line_form) {
     if (batch == 0) return;
+    if (cluster_plane(n)) return zlines_reg(W, batch, kind, line_form, kscale, ecut, tw, st);
     SGW_DISPATCH_ROWS(n, {
         const dim3 grid((N / LT) * N, batch);
         if (kind == 0)
@@ -429,9 +367,10 @@ void rows_zlines_energy(int n, const float2* W, int batch, float kscale, const f
 }
 
 // The W input of the step is transformed back along y in place (the plane path leaves it intact;
-// every caller overwrites W afterwards).
-void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st) {
+// every caller overwrites W afterwards).  At 288 one cluster of CTAs per plane does the whole pass.
+void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
     if (batch == 0) return;
+    if (cluster_plane(n)) return cplane_step(a, batch, tw, st, variant);
     ylines(n, const_cast<float2*>(a.W), batch, +1, tw, st);
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     SGW_DISPATCH_ROWS(n, k_rows_step<N><<<dim3(N * N / RR, batch), RNT, rows_step_smem(N, slots), st>>>(a, tw));

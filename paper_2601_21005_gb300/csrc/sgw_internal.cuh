@@ -99,8 +99,10 @@ cudaError_t plane_step_reserve_smem(int n, int max_plane_slots);
 int pencil_blocks_per_sm(int n);
 void launch_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st);
 // kind: 0 kinetic (T(k)/N^3, capped at ecut if ecut > 0), 1 Coulomb (4 pi/k^2 / N^3, k=0 -> 0)
+// line_form: form of the z-line pass on the 288 grid (0, 1, 2; a launch hint)
 void launch_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw,
-                   cudaStream_t st, int pf_ahead = 0, const VecInfo* info = nullptr, float dt = 0.f);
+                   cudaStream_t st, int pf_ahead = 0, const VecInfo* info = nullptr, float dt = 0.f,
+                   int line_form = 0);
 void launch_plane_fwd_phase(int n, const float2* psi, const float* vpot, const float* dvpot, const VecInfo* info,
                             float dt, float2* W, int batch, const float2* tw, cudaStream_t st);
 void launch_split_tangent(float2* psi, const float* dvpot, const VecInfo* info, float dt, int batch, int64_t ng,
@@ -137,17 +139,32 @@ int rows_units(int n);
 size_t rows_step_smem(int n, int max_unit_slots);
 cudaError_t rows_init_attributes(int n);
 cudaError_t rows_step_reserve_smem(int n, int max_unit_slots);
-int rows_step_blocks_per_sm(int n, int max_unit_slots);
+int rows_step_blocks_per_sm(int n, int variant, int max_unit_slots);
 int zlines_blocks_per_sm(int n);
 void rows_plane_fwd(int n, const float2* in, float2* W, int batch, const float2* tw, cudaStream_t st);
-void rows_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st);
+void rows_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st,
+                 int line_form);
 void rows_zlines_energy(int n, const float2* W, int batch, float kscale, const float2* tw, double* part,
                         cudaStream_t st);
-void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st);
+void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant);
 void rows_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c, const float* vloc,
                     float* vtot, float* dv, float* uR, int64_t uR_stride, float* out_re, cudaStream_t st);
 void rows_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0, int store_rho0,
                       float2* Wp, const float2* tw, cudaStream_t st);
+
+// ---- the 288 grid (kernels_cluster.cu): one thread-block cluster of 8 CTAs per xy plane for the
+// fused step (units of 36 rows), z lines in one of three forms
+bool cluster_plane(int n);
+int cluster_unit_rows();
+size_t cplane_smem(int max_unit_slots);
+cudaError_t cluster_init_attributes(int max_unit_slots);
+int cplane_blocks_per_sm(int variant, int max_unit_slots);
+int zlines_reg_blocks_per_sm(int form);
+// variant 0: the row form (y lines, 36-row step, y lines); 1, 2: one cluster of 8 CTAs per plane
+// with 32 / 18 warps per CTA
+void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant);
+// form 0 / 1: register-ended Stockham tiles of 16 / 32 columns, 2: warp-FFT tiles of 16 columns
+void zlines_reg(float2* W, int batch, int kind, int form, float kscale, float ecut, const float2* tw, cudaStream_t st);
 
 // ---- other kernels (kernels_misc.cu)
 void launch_noise(int ng, uint64_t seed, uint32_t stream_id, int sample0, int n_samples, int n_vec,

@@ -25,7 +25,8 @@ def main():
     ap.add_argument('--radius', type=float, default=None,
                     help='cluster radius in bohr (default 10.5 = Si35H36; 28.0 = Si657H300 at n = 128)')
     ap.add_argument('--tune', default=None,
-                    help='semicolon-separated settings "operands,plane_lookahead,pencil_lookahead" to time in turn')
+                    help='semicolon-separated settings "operands,plane_lookahead,pencil_lookahead,variant,line_tile" '
+                         '(a prefix of the tuning keys) to time in turn')
     ap.add_argument('--autotune', action='store_true', help='run the library autotuner first and report its choice')
     ap.add_argument('--split', action='store_true', help='time the split-operator propagator instead of Chebyshev')
     args = ap.parse_args()

@@ -296,7 +296,8 @@ class Context:
     def set_graph_mode(self, enable):
         self._ck('sgw_set_graph_mode', lib().sgw_set_graph_mode(self._p, 1 if enable else 0))
 
-    TUNE_PLANE_OPERANDS, TUNE_PLANE_LOOKAHEAD, TUNE_PENCIL_LOOKAHEAD, TUNE_PLANE_VARIANT, TUNE_KEYS = 0, 1, 2, 3, 4
+    (TUNE_PLANE_OPERANDS, TUNE_PLANE_LOOKAHEAD, TUNE_PENCIL_LOOKAHEAD, TUNE_PLANE_VARIANT, TUNE_LINE_FORM,
+     TUNE_KEYS) = 0, 1, 2, 3, 4, 5
 
     def set_tuning(self, key, value):
         self._ck('sgw_set_tuning', lib().sgw_set_tuning(self._p, int(key), int(value)))
