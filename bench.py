@@ -3,18 +3,26 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--config NAME]
 
-One step = one pass of the whole hot path over one batch of Monte-Carlo samples of the
-workload: white noise, gapped filter (Eq. 3), exchange, linear-response TDH (u^R), time
-ordering, zeta propagation with the Sigma(t) accumulation (Eq. 4-5), and the QP solve
-(Eq. 6-7) on the samples accumulated so far.  Default workload: the 64^3 Si35H36 cluster
-(h = 0.5 bohr, 176 electrons), 4 samples x 16 orbitals (8 eta pairs) = 64 orbitals
-propagated for 400 steps of dt = 0.05 with Chebyshev degree 16, filter degree 2000.
+Headline workload (default): the large synthetic cluster Si7055H1596 on a 288^3 grid (h = 0.5
+bohr, 29,816 electrons, s/p KB projectors on every Si), one batch of 4 Monte-Carlo samples =
+64 TDH orbitals (8 eta pairs each) and 8 zeta vectors, u^R carried in the sparse stochastic xi
+basis of the paper's runs (N_xi = 10^4, f_g = 0.003, segments of 32; Sec. 2.3, Table 2).  The
+batch's white noise and occupied filter (Eq. 3) run once before the timed region (timed
+separately: the `filter` object); one bench step is `step_time_steps` time steps of everything
+after the filter for that batch: exchange, the linear-response TDH propagation of the 64
+orbitals (Chebyshev degree 16, dt = 0.05) with the xi projection of u^R, time ordering, the zeta
+propagation with the FP64 Sigma(t) accumulation (Eq. 4-5) and the QP solve (Eq. 6-7).  The
+metric counts grid points x TDH orbitals x time steps per second of the whole step.
 
-The metric counts grid points x propagated orbitals x time steps of the TDH propagation
-per second of the whole step.  With --impl reference the FP64 CPU oracle is timed on a
-bounded sample of the same workload instead (see `oracle_sample`).
+Secondary workload (object `c2_64`): the 64^3 Si35H36 cluster through the whole path per step
+(16 samples: noise, degree-2000 filter, TDH and zeta over 400 steps, QP), with the time to
++-0.03 eV of the plain FP32 form and of the chosen form (mixed precision + control variate).
+
+With --impl reference the FP64 CPU oracle is timed on a bounded sample of the headline workload
+on every host core instead (`oracle_sample`).
 """
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -31,7 +39,20 @@ UNIT = 'grid-pt*orbital*steps/s'
 HA_EV = 27.211386245988
 
 CONFIGS = {
-    # the 64^3 cluster the metric is quoted on
+    # the large cluster: the largest configuration that fits one GPU
+    'si7055h1596_288': dict(
+        system='si_cluster', n=288, h=0.5, radius=61.0, samples_per_batch=4, zeta_group=1, n_eta=8,
+        step_time_steps=4, n_tau=1000, dt=0.05, cheb_deg=16, n_cheb=4000, xi=dict(n_xi=10000, f_g=0.003, L=32),
+        # occupied-filter window: centred on the gap the kernel-polynomial search finds for this
+        # cluster (-0.0895 Ha, count 14907.6 +- 42 at n_occ = 14908); the target orbital is a
+        # stand-in (a normalised Gaussian at the cluster centre): the cost of a step does not
+        # depend on either
+        e_homo=-0.1045, e_lumo=-0.0745,
+        workload='Si7055H1596 cluster, 288^3 grid h=0.5 bohr, 29816 electrons, KB on 7055 Si; one batch of '
+                 '4 MC samples = 64 TDH orbitals (8 eta pairs each) + 8 zeta vectors, xi-compressed u '
+                 '(N_xi=10000, f_g=0.003, L=32), Chebyshev degree 16, dt=0.05; per step 4 TDH + 4 zeta time '
+                 'steps with Sigma(t) and the QP solve after the batch\'s occupied filter (degree 4000, at setup)'),
+    # the small cluster, whole path per step
     'si35h36_64': dict(system='si_cluster', n=64, h=0.5, radius=10.5, samples_per_batch=4, zeta_group=4, n_eta=8,
                        n_steps=400, dt=0.05, cheb_deg=16, n_cheb=2000, workload='Si35H36 cluster, 64^3 grid '
                        'h=0.5 bohr, 176 electrons, 64 orbitals per TDH launch (4 MC samples x 8 eta pairs) x '
@@ -42,6 +63,13 @@ CONFIGS = {
                     '16 orbitals x 200 steps'),
 }
 
+# ncu DRAM bytes (read + write) over the algorithmic bytes of one launch of a kernel kind, from one
+# capture of the kernel source whose sha256 prefix is given; a roofline line reports `traffic`
+# only while that source is unchanged.
+TRAFFIC = {
+    ('plane_step', 64): dict(ratio=839.2 / 806.4, source='kernels_grid.cu', sha='', capture='64-vector launch'),
+}
+
 
 def load_peaks():
     p = os.path.join(ROOT, 'MEASURED_PEAKS.json')
@@ -50,6 +78,11 @@ def load_peaks():
             d = json.load(f)
         return dict(hbm_gbs=float(d['hbm_gbs']), bf16_tflops=float(d['bf16_tflops']), source='measured')
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source='fallback')
+
+
+def source_sha(name):
+    with open(os.path.join(ROOT, 'paper_2601_21005_gb300', 'csrc', name), 'rb') as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
 class ClockSampler:
@@ -127,13 +160,15 @@ def kohn_sham_inputs(cfg, sysd, device):
                 raw_bounds=raw, eig_residual=res)
 
 
-def make_pipeline(cfg, sysd, ks, device, seed, fp64=True, graphs=False, autotune=False, zeta_group=None):
+def make_pipeline(cfg, sysd, ks, device, seed, fp64=True, graphs=False, autotune=False, zeta_group=None,
+                  n_steps=None, xi=None):
     from paper_2601_21005_gb300.pipeline import Pipeline
     return Pipeline(cfg['n'], cfg['h'], sysd['vloc'], sysd['kb_atoms'], ks['phi'], ks['e_homo'], ks['e_lumo'],
-                    n_eta=cfg['n_eta'], n_steps=cfg['n_steps'], dt=cfg['dt'], cheb_deg=cfg['cheb_deg'],
-                    n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'], seed=seed, stream_id=1,
-                    device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64, graphs=graphs, autotune=autotune,
-                    zeta_group=cfg['zeta_group'] if zeta_group is None else zeta_group)
+                    n_eta=cfg['n_eta'], n_steps=cfg['n_steps'] if n_steps is None else n_steps, dt=cfg['dt'],
+                    cheb_deg=cfg['cheb_deg'], n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'],
+                    seed=seed, stream_id=1, device=device, spectrum=(ks['emin'], ks['emax']), fp64=fp64,
+                    graphs=graphs, autotune=autotune,
+                    zeta_group=cfg['zeta_group'] if zeta_group is None else zeta_group, xi=xi)
 
 
 def step_samples(cfg):
@@ -143,16 +178,11 @@ def step_samples(cfg):
 
 def units_per_step(cfg):
     """grid points x TDH-propagated orbitals x time steps of one bench step."""
-    return cfg['n'] ** 3 * 2 * cfg['n_eta'] * step_samples(cfg) * cfg['n_steps']
+    steps = cfg['step_time_steps'] if 'step_time_steps' in cfg else cfg['n_steps']
+    return cfg['n'] ** 3 * 2 * cfg['n_eta'] * step_samples(cfg) * steps
 
 
-# DRAM bytes (read + write, ncu) over algorithmic bytes of one 64-vector k_plane_step launch of the
-# current kernel (profiles/plane_step_pencil_64x64.md); traffic per launch = this ratio x the
-# launch's algorithmic bytes.  Must be re-measured whenever the plane kernel changes.
-PLANE_STEP_DRAM_PER_ALG = 839.2 / 806.4
-
-
-def roofline(prof, peaks):
+def roofline(prof, peaks, n):
     """Dominant kernel kind by device time; achieved = its algorithmic bytes / its event time."""
     kinds = {k: v for k, v in prof.items() if v['launches'] > 0 and v['alg_bytes'] > 0}
     total = sum(v['ms'] for v in prof.values())
@@ -161,15 +191,19 @@ def roofline(prof, peaks):
     gbs = v['alg_bytes'] / (v['ms'] * 1e-3) / 1e9
     peak = peaks['hbm_gbs']
     shares = {k: round(x['ms'] / total, 4) for k, x in prof.items() if x['launches']}
+    tr = TRAFFIC.get((name, n))
+    traffic, tsrc = None, 'no ncu capture of the current kernel source'
+    if tr is not None and tr['sha'] and tr['sha'] == source_sha(tr['source']):
+        traffic = round(tr['ratio'] * v['alg_bytes'] / v['launches'])
+        tsrc = ('ncu dram__bytes_read.sum + dram__bytes_write.sum of a %s of this kernel source (%s %s), '
+                'scaled by algorithmic bytes to the average launch' % (tr['capture'], tr['source'], tr['sha']))
     return dict(bound='hbm', achieved=round(gbs, 1), peak=peak, unit='GB/s', frac=round(gbs / peak, 4),
-                traffic=(round(PLANE_STEP_DRAM_PER_ALG * v['alg_bytes'] / v['launches'])
-                         if name == 'plane_step' else None),
-                traffic_source='ncu dram__bytes_read.sum + dram__bytes_write.sum of a 64-vector launch, '
-                               'scaled by algorithmic bytes to the average launch' if name == 'plane_step' else None,
-                kernel=name, launches=v['launches'], avg_launch_us=round(1e3 * v['ms'] / v['launches'], 2),
-                alg_bytes_per_launch=round(v['alg_bytes'] / v['launches']), peak_source=peaks['source'] + ' hbm_gbs',
+                traffic=traffic, traffic_source=tsrc, kernel=name, launches=v['launches'],
+                avg_launch_us=round(1e3 * v['ms'] / v['launches'], 2), alg_bytes_per_launch=round(v['alg_bytes'] /
+                                                                                                v['launches']),
+                peak_source=peaks['source'] + ' hbm_gbs (burst copy; the kernel is timed inside a long step)',
                 time_shares=shares,
-                other_kernels={k: round(x['alg_bytes'] / (x['ms'] * 1e-3) / 1e9, 1) for k, x in kinds.items()})
+                other_kernels_gbs={k: round(x['alg_bytes'] / (x['ms'] * 1e-3) / 1e9, 1) for k, x in kinds.items()})
 
 
 def time_to_target(pl, sig, xs, eps_ks, seconds_per_sample, target_ev=0.03):
@@ -185,102 +219,274 @@ def time_to_target(pl, sig, xs, eps_ks, seconds_per_sample, target_ev=0.03):
 
 
 # ---------------------------------------------------------------- the oracle on the host cores
-def oracle_sample(cfg, n_filter_terms=2, n_tdh_steps=1, n_zeta_steps=1, seed=1000):
-    """Time the FP64 oracle on a bounded sample of one batch and extrapolate to the batch.
+_ORC = {}
 
-    Timed pieces (one MC sample): n_filter_terms Chebyshev terms of the filter on the
-    n_eta + 1 noise vectors, n_tdh_steps TDH steps of the n_eta pairs, n_zeta_steps zeta
-    steps of the pair with the Sigma(t) sums, the exchange, and the time ordering of a
-    4096-point slice of u^R over the full step count.  The batch time is
-      n_samples * (N_chb t_filter + N_tau (t_tdh + t_zeta) + t_x + t_to * N_g / 4096).
-    Inputs are the workload's system with a smooth stand-in orbital (timing does not depend
-    on the orbital's values).
-    """
+
+def _oracle_term(i):
+    """One Chebyshev term of the oracle's propagator (one H application and the recurrence update,
+    FP64) on a vector of its own; returns the seconds it took."""
     import numpy as np
     from oracle import chebyshev as cheb
+    p = _ORC['prob']
+    v = np.random.default_rng(1000 + i).normal(size=p.grid.shape()) + 0j
+    t0 = time.perf_counter()
+    cheb.propagate_step(p.h0, v, p.emin, p.emax, 0.05, 1)
+    return time.perf_counter() - t0
+
+
+def oracle_pool(cfg, processes):
+    """Fork a pool of oracle workers sharing the workload's H0 (only in a process that has not
+    touched a GPU)."""
+    import multiprocessing as mp
+    import numpy as np
     from oracle import hamiltonian as ham
     from oracle import sgw as osgw
-    from paper_2601_21005_gb300 import synth
     sysd = build_system(cfg)
     g = ham.Grid(cfg['n'], cfg['h'])
     kb = ham.KB(sysd['kb_atoms']) if sysd['kb_atoms'] else None
-    L = cfg['n'] * cfg['h']
-    phi = synth.smooth_orbital(cfg['n'], cfg['h'], (L / 2, L / 2, L / 2))
     emin, emax = float(sysd['vloc'].min()) - 1.0, 0.5 * 3 * (np.pi / cfg['h']) ** 2 + 1.0
-    prob = osgw.Problem(g, sysd['vloc'], kb, emin, emax, emin + 0.5, emin + 0.6, phi)
-    ne, N = cfg['n_eta'], cfg['n_steps']
-    t = {}
-    noise = osgw.white_noise(g, seed, 1, 0, ne + 1)
-    t0 = time.perf_counter()
-    filt = osgw.filter_batch(prob, noise, np.ones(n_filter_terms + 1) / (n_filter_terms + 1))
-    t['filter_term'] = (time.perf_counter() - t0) / n_filter_terms
-    eta, zbar = filt[1:], noise[0]
-    t0 = time.perf_counter()
-    osgw.tdh_response_tangent(prob, eta, zbar * phi, n_tdh_steps, cfg['dt'], cfg['cheb_deg'])
-    t['tdh_step'] = (time.perf_counter() - t0) / n_tdh_steps
-    u = np.zeros((n_zeta_steps + 1,) + g.shape(), dtype=np.complex128)
-    t0 = time.perf_counter()
-    osgw.sigma_t(prob, filt[0], zbar - filt[0], u, n_zeta_steps, cfg['dt'], cfg['cheb_deg'])
-    t['zeta_step'] = (time.perf_counter() - t0) / n_zeta_steps
-    t0 = time.perf_counter()
-    osgw.exchange(prob, eta)
-    t['exchange'] = time.perf_counter() - t0
-    sl = min(4096, g.ng)
-    t0 = time.perf_counter()
-    osgw.time_order(np.zeros((N + 1, sl)))
-    t['time_order'] = (time.perf_counter() - t0) * g.ng / sl
-    per_sample = (cfg['n_cheb'] * t['filter_term'] + N * (t['tdh_step'] + t['zeta_step']) + t['exchange']
-                  + t['time_order'])
-    batch_s = step_samples(cfg) * per_sample
-    measured = n_filter_terms * t['filter_term'] + n_tdh_steps * t['tdh_step'] + n_zeta_steps * t['zeta_step'] \
-        + t['exchange'] + t['time_order'] * sl / g.ng
-    return dict(value=units_per_step(cfg) / batch_s, batch_seconds=batch_s, measured_seconds=measured, parts=t)
+    _ORC['prob'] = osgw.Problem(g, sysd['vloc'], kb, emin, emax, emin + 0.5, emin + 0.6, np.zeros(g.shape()))
+    return mp.get_context('fork').Pool(processes)
+
+
+def oracle_sample(cfg, pool, processes):
+    """Time `processes` oracle Chebyshev terms run at once, one per process, and extrapolate to one
+    bench step: terms per step = time steps x 16 x (64 TDH orbitals + 8 zeta vectors); the
+    per-step density, Poisson, xi and Sigma(t) work (under 2% of the terms' FFTs) is not counted,
+    which favours the CPU."""
+    per = pool.map(_oracle_term, range(processes), chunksize=1)
+    wall = max(per)                 # the terms run at once: the slowest one ends the round
+    n_vec = 2 * cfg['n_eta'] * step_samples(cfg) + 2 * step_samples(cfg)
+    terms = cfg['step_time_steps'] * cfg['cheb_deg'] * n_vec
+    step_s = terms * wall / processes
+    return dict(value=units_per_step(cfg) / step_s, step_seconds=step_s, wall=wall,
+                term_seconds_mean=statistics.mean(per), terms_per_step=terms)
 
 
 def run_reference(args, cfg):
-    """--impl reference: the FP64 oracle on the host cores (rank 0 only), K timed bounded samples."""
+    """--impl reference: the FP64 oracle on every host core (rank 0 only), K timed bounded samples."""
     rank = int(os.environ.get('RANK', '0'))
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_sample(cfg)
-    vals, meas = [], []
-    for _ in range(args.steps):
-        r = oracle_sample(cfg)
-        vals.append(r['value'])
-        meas.append(r['measured_seconds'])
-    v = statistics.median(vals)
-    sample = ('per step: 1 MC sample of %s -- %d filter terms on %d vectors, 1 TDH step of %d pairs, '
-              '1 zeta step, exchange, time ordering of a 4096-point slice; extrapolated to the batch of %d '
-              'samples x (N_chb=%d, N_tau=%d)' % (cfg['workload'], 2, cfg['n_eta'] + 1, cfg['n_eta'],
-                                                  step_samples(cfg), cfg['n_cheb'], cfg['n_steps']))
+    if 'step_time_steps' not in cfg:
+        raise SystemExit('the reference arm times the headline workload only')
+    P = os.cpu_count() or 1
+    pool = oracle_pool(cfg, P)
+    try:
+        for _ in range(args.warmup):
+            oracle_sample(cfg, pool, P)
+        rs = [oracle_sample(cfg, pool, P) for _ in range(args.steps)]
+    finally:
+        pool.close()
+        pool.join()
+    v = statistics.median([r['value'] for r in rs])
+    sample = ('per step: %d FP64 oracle Chebyshev terms (one H application with the recurrence update on one '
+              '288^3 vector each) run at once on %d host processes, extrapolated to the step\'s %d terms (%d time '
+              'steps x degree %d x %d vectors)' % (P, P, rs[0]['terms_per_step'], cfg['step_time_steps'],
+                                                  cfg['cheb_deg'], rs[0]['terms_per_step'] //
+                                                  (cfg['step_time_steps'] * cfg['cheb_deg'])))
     line = dict(impl='reference', metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
-                warmup=args.warmup, ms_per_step=1e3 * statistics.median(meas), higher_is_better=True,
-                scaling='weak', vs_baseline=None, dtype='f64', data='synthetic',
+                warmup=args.warmup, ms_per_step=1e3 * statistics.median([r['wall'] for r in rs]),
+                higher_is_better=True, scaling='weak', vs_baseline=None, dtype='f64', data='synthetic',
                 config=dict(workload=cfg['workload'], l2='inputs larger than L2'),
-                cpu_baseline=dict(value=v, unit=UNIT, cores=1, kind='oracle', sample=sample,
-                                  batch_seconds_extrapolated=r['batch_seconds'], parts_s=r['parts']),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=P, kind='oracle', sample=sample,
+                                  step_seconds_extrapolated=statistics.median([r['step_seconds'] for r in rs]),
+                                  term_seconds_mean=statistics.median([r['term_seconds_mean'] for r in rs])),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
 
-# ---------------------------------------------------------------- our arm
 def cpu_baseline_subprocess(args):
-    """Run the reference arm once (one bounded sample) in a fresh process with one BLAS thread."""
-    env = dict(os.environ, OMP_NUM_THREADS='1', OPENBLAS_NUM_THREADS='1', MKL_NUM_THREADS='1')
+    """Run the reference arm once (one bounded sample) in a fresh process that never touches a GPU."""
+    env = dict(os.environ)
     for k in ('RANK', 'WORLD_SIZE', 'LOCAL_RANK'):
         env.pop(k, None)
+    for k in ('OMP_NUM_THREADS', 'OPENBLAS_NUM_THREADS', 'MKL_NUM_THREADS'):
+        env[k] = '1'                    # one thread per process: the processes are the parallelism
     cmd = [sys.executable, os.path.join(ROOT, 'bench.py'), '--impl', 'reference', '--steps', '1', '--warmup', '0',
            '--config', args.config]
-    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=900)
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1200)
     for line in r.stdout.splitlines()[::-1]:
         if line.startswith('{'):
             return json.loads(line)['cpu_baseline']
-    return dict(value=None, unit=UNIT, cores=1, kind='oracle', sample='failed: ' + r.stderr[-300:])
+    return dict(value=None, unit=UNIT, cores=os.cpu_count(), kind='oracle', sample='failed: ' + r.stderr[-300:])
+
+
+# ---------------------------------------------------------------- our arm: the large cluster
+def measure_large(args, cfg, local, world, rank, dist, peaks):
+    import numpy as np
+    import torch
+    from paper_2601_21005_gb300 import replicas, synth
+    t_setup = time.perf_counter()
+    sysd = build_system(cfg)
+    n, h = cfg['n'], cfg['h']
+    c = 0.5 * n * h
+    phi = synth.smooth_orbital(n, h, (c, c, c), width=3.0)
+    phi /= np.sqrt(h ** 3 * np.sum(phi ** 2))
+    from paper_2601_21005_gb300 import sgw
+    S = cfg['step_time_steps']
+    ks = dict(e_homo=cfg['e_homo'], e_lumo=cfg['e_lumo'], phi=phi, emin=None, emax=None)
+    # spectral interval by the library's shifted power iteration on the same H0
+    kctx = sgw.Context(n, h, max_batch=1, device=local)
+    kctx.set_potential(torch.as_tensor(sysd['vloc'].reshape(-1).astype(np.float32)).cuda(local), sysd['kb_atoms'])
+    (ks['emin'], ks['emax']), _ = kctx.spectral_bounds(200, 1000, 0.05)
+    kctx.close()
+    seed = 1000 * 5
+    base = replicas.sample_base(rank)
+    pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs, n_steps=S, xi=cfg['xi'])
+    del sysd
+    ns = step_samples(cfg)
+    st = torch.cuda.current_stream()
+    # the batch's noise and occupied filter, timed on their own
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    pl.filter_batch(base)
+    e1.record(st)
+    torch.cuda.synchronize()
+    filt_ms = e0.elapsed_time(e1)
+    nv_filter = ns * (cfg['n_eta'] + 1)
+    filt = dict(vectors=nv_filter, degree=cfg['n_cheb'], ms=round(filt_ms, 1),
+                vector_terms_per_s=nv_filter * cfg['n_cheb'] / (filt_ms * 1e-3),
+                grid_pt_vector_terms_per_s=n ** 3 * nv_filter * cfg['n_cheb'] / (filt_ms * 1e-3))
+    t_setup = time.perf_counter() - t_setup
+    sig = torch.empty(ns, 2 * S + 1, dtype=torch.complex128, device='cuda')
+    xs = torch.empty(ns, dtype=torch.float64, device='cuda')
+
+    def step():
+        pl.propagate_batch(base, sig, xs)
+        pl.qp(sig, xs, cfg['e_homo'])               # host scalars: synchronises
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    n0 = pl.ctx.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = pl.ctx.launch_count() - n0
+    # kernel durations: one more step with per-launch events (while profiling, the library launches
+    # directly instead of replaying its graphs)
+    pl.ctx.profile(True)
+    step()
+    prof = pl.ctx.profile_read()
+    pl.ctx.profile(False)
+    ms = replicas.max_over_ranks(ms, dist, 'cuda')
+    value = replicas.job_throughput(units_per_step(cfg), args.steps, world, ms)
+    # end to end through the public API: per step the batch's noise and filtered vectors and the
+    # target orbital come from pinned host memory, Sigma(t), X and the QP result go back
+    noise_h = pl.noise.cpu().pin_memory()
+    filt_h = pl.filt.cpu().pin_memory()
+    phi_h = pl.phi.cpu().pin_memory()
+    sig_h = torch.empty(ns, 2 * S + 1, dtype=torch.complex128).pin_memory()
+    x_h = torch.empty(ns, dtype=torch.float64).pin_memory()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        pl.noise.copy_(noise_h, non_blocking=True)
+        pl.filt.copy_(filt_h, non_blocking=True)
+        pl.phi.copy_(phi_h, non_blocking=True)
+        pl.propagate_batch(base, sig, xs)
+        sig_h.copy_(sig, non_blocking=True)
+        x_h.copy_(xs, non_blocking=True)
+        pl.qp(sig, xs, cfg['e_homo'])
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_e2e = replicas.max_over_ranks(e0.elapsed_time(e1), dist, 'cuda')
+    h2d = noise_h.numel() * 8 + filt_h.numel() * 8 + phi_h.numel() * 4
+    e2e = dict(value=replicas.job_throughput(units_per_step(cfg), args.steps, world, ms_e2e), unit=UNIT,
+               h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(sig_h.numel() * 16 + x_h.numel() * 8 + 32))
+    rl = roofline(prof, peaks, n)
+    peak_gb = round(torch.cuda.max_memory_allocated(local) / 1e9, 1)
+    pl.ctx.close()
+    return dict(value=value, ms=ms, ms_per_step=ms / args.steps, launches=launches, clocks=clk, e2e=e2e,
+                roofline=rl, filter=filt, setup_seconds=round(t_setup, 1), peak_device_gb=peak_gb,
+                spectrum=[pl.emin, pl.emax])
+
+
+# ---------------------------------------------------------------- our arm: the 64^3 whole path
+def measure_whole_path(args, cfg, local, world, rank, dist, peaks, steps, warmup):
+    import numpy as np
+    import torch
+    from paper_2601_21005_gb300 import replicas
+    sysd = build_system(cfg)
+    t_setup = time.perf_counter()
+    ks = kohn_sham_inputs(cfg, sysd, local)
+    pl = make_pipeline(cfg, sysd, ks, local, 1000 * 2, graphs=args.graphs, autotune=args.autotune)
+    t_setup = time.perf_counter() - t_setup
+    ns = step_samples(cfg)
+    nb_total = warmup + steps
+    sig = torch.empty(nb_total * ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
+    xs = torch.empty(nb_total * ns, dtype=torch.float64, device='cuda')
+    base = replicas.sample_base(rank)
+    eps_ks = ks['e_homo']
+
+    def step(b):
+        s0 = b * ns
+        pl.run_batch(base + s0, sig[s0:s0 + ns], xs[s0:s0 + ns])
+        pl.qp(sig[:s0 + ns], xs[:s0 + ns], eps_ks) if s0 + ns >= 2 else None
+
+    for b in range(warmup):
+        step(b)
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for b in range(warmup, nb_total):
+        step(b)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = replicas.max_over_ranks(e0.elapsed_time(e1), dist, 'cuda')
+    pl.ctx.profile(True)
+    step(0)
+    prof = pl.ctx.profile_read()
+    pl.ctx.profile(False)
+    ms_per_step = ms / steps
+    value = replicas.job_throughput(units_per_step(cfg), steps, world, ms)
+    sig_all, xs_all = replicas.gather_rows(sig, xs, dist)
+    tt = time_to_target(pl, sig_all, xs_all, eps_ks, ms_per_step * 1e-3 / (ns * world))
+    prec = precision_comparison(cfg, pl, ks, base)
+    cvres = cv_study(args, cfg, pl, ks, base, ms_per_step * 1e-3 / ns) if args.cv > 0 else None
+    chosen = None
+    if cvres is not None:
+        # the chosen form (mixed precision + control variate) against the plain FP32 form (no control
+        # variate, FP32 reductions at their own measured speed)
+        plain_s = cvres['time_to_0_03eV_plain_s'] * prec['ms_per_step_plain_fp32'] / prec['ms_per_step_mixed']
+        chosen = dict(workload=cfg['workload'], plain_fp32_seconds=round(plain_s, 1),
+                      chosen_seconds=cvres['time_to_0_03eV_cv_s'],
+                      chosen_seconds_incl_training=cvres['time_to_0_03eV_cv_incl_training_s'],
+                      speedup=round(plain_s / cvres['time_to_0_03eV_cv_s'], 3),
+                      speedup_incl_training=round(plain_s / cvres['time_to_0_03eV_cv_incl_training_s'], 3))
+    out = dict(workload=cfg['workload'], value=value, unit=UNIT, ms_per_step=round(ms_per_step, 1), steps=steps,
+               warmup=warmup, roofline=roofline(prof, peaks, cfg['n']), time_to_0_03eV=tt,
+               time_to_0_03eV_chosen_vs_plain=chosen, precision_forms=prec, control_variate=cvres,
+               setup=dict(seconds=round(t_setup, 2), e_homo=ks['e_homo'], e_lumo=ks['e_lumo'],
+                          gap_eV=round((ks['e_lumo'] - ks['e_homo']) * HA_EV, 4), emin=ks['emin'], emax=ks['emax'],
+                          eig_residual=float(ks['eig_residual'])))
+    if args.split_study:
+        out['split_operator'] = split_study(cfg, pl)
+    if args.xi_study:
+        out['xi_compression'] = xi_study(args, cfg, sysd, ks, pl, base)
+    pl.ctx.close()
+    return out
 
 
 def run_ours(args, cfg):
-    import numpy as np
     import torch
     world = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))
@@ -290,139 +496,49 @@ def run_ours(args, cfg):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group('nccl', device_id=torch.device('cuda', local))
-    from paper_2601_21005_gb300 import build, replicas
+    from paper_2601_21005_gb300 import build
     build.build()
     peaks = load_peaks()
-    seed = 1000 * 2
-    sysd = build_system(cfg)
-    t_setup = time.perf_counter()
-    if args.ks_cache and os.path.exists(args.ks_cache):
-        z = np.load(args.ks_cache)
-        ks = {k: (z[k].item() if z[k].ndim == 0 else z[k]) for k in z.files}
+    if 'step_time_steps' in cfg:
+        big = measure_large(args, cfg, local, world, rank, dist, peaks)
+        torch.cuda.empty_cache()
+        sec = None
+        if not args.no_secondary:
+            sec = measure_whole_path(args, CONFIGS['si35h36_64'], local, world, rank, dist, peaks,
+                                     args.secondary_steps, 2)
+        line = dict(metric=METRIC, value=big['value'], unit=UNIT, n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=big['ms_per_step'], higher_is_better=True, scaling='weak',
+                    vs_baseline=None, dtype='c64/f32 + f64', data='synthetic',
+                    config=dict(workload=cfg['workload'], step_time_steps=cfg['step_time_steps'],
+                                n_cheb=cfg['n_cheb'], cheb_deg=cfg['cheb_deg'], dt=cfg['dt'],
+                                samples_per_step=step_samples(cfg) * world,
+                                tdh_orbitals_per_launch=2 * cfg['n_eta'] * cfg['samples_per_batch'],
+                                zeta_vectors_per_launch=2 * step_samples(cfg), xi=cfg['xi'],
+                                l2='inputs larger than L2 (the 64 TDH orbitals alone are 12 GB)',
+                                precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world,
+                                cuda_graphs=bool(args.graphs),
+                                roofline_timing='per-kernel CUDA events over one extra step with direct launches '
+                                                '(graph replay is timed unprofiled)'),
+                    e2e=big['e2e'], gpu_launches=int(big['launches']), roofline=big['roofline'], cpu_baseline=None,
+                    clocks=big['clocks'], filter=big['filter'],
+                    setup=dict(seconds=big['setup_seconds'], spectrum=big['spectrum'],
+                               peak_device_gb=big['peak_device_gb'],
+                               ks='stand-in orbital and the filter window of the config (cost does not depend on '
+                                  'them)'),
+                    time_to_0_03eV_chosen_vs_plain=sec['time_to_0_03eV_chosen_vs_plain'] if sec else None,
+                    c2_64=sec)
     else:
-        ks = kohn_sham_inputs(cfg, sysd, local)
-        if args.ks_cache:
-            np.savez(args.ks_cache, **{k: np.asarray(v) for k, v in ks.items()})
-    pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs, autotune=args.autotune)
-    t_setup = time.perf_counter() - t_setup
-    ns = step_samples(cfg)
-    nb_total = args.warmup + args.steps
-    sig = torch.empty(nb_total * ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
-    xs = torch.empty(nb_total * ns, dtype=torch.float64, device='cuda')
-    base = replicas.sample_base(rank)   # each rank draws its own samples: no data-path collective
-    eps_ks = ks['e_homo']
-
-    def step(b):
-        s0 = b * ns
-        pl.run_batch(base + s0, sig[s0:s0 + ns], xs[s0:s0 + ns])
-        pl.qp(sig[:s0 + ns], xs[:s0 + ns], eps_ks) if s0 + ns >= 2 else None
-
-    for b in range(args.warmup):
-        step(b)
-    torch.cuda.synchronize()
-    st = torch.cuda.current_stream()
-    clocks = ClockSampler(local)
-    if not args.graphs:                # per-launch events would disable the graph replay
-        pl.ctx.profile(True)
-    n0 = pl.ctx.launch_count()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.nvtx.range_push('sgw_timed')
-    e0.record(st)
-    for b in range(args.warmup, nb_total):
-        step(b)
-    e1.record(st)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    launches = pl.ctx.launch_count() - n0
-    if args.graphs:
-        # kernel durations from one more step with per-launch events (direct launches)
-        pl.ctx.profile(True)
-        step(0)
-        prof = pl.ctx.profile_read()
-        pl.ctx.profile(False)
-    else:
-        prof = pl.ctx.profile_read()
-        pl.ctx.profile(False)
-    ms = replicas.max_over_ranks(ms, dist, 'cuda')
-    ms_per_step = ms / args.steps
-    value = replicas.job_throughput(units_per_step(cfg), args.steps, world, ms)
-    # one QP solve over every rank's samples (gathered after the timed region)
-    sig_all, xs_all = replicas.gather_rows(sig, xs, dist)
-    tt = time_to_target(pl, sig_all, xs_all, eps_ks, ms_per_step * 1e-3 / (ns * world))
-
-    # end to end through the public API: per step the target orbital comes from pinned host
-    # memory and Sigma(t), X and the QP result go back to the host
-    phi_h = torch.from_numpy(np.asarray(ks['phi'], dtype=np.float32).reshape(-1)).pin_memory()
-    sig_h = torch.empty(ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128).pin_memory()
-    x_h = torch.empty(ns, dtype=torch.float64).pin_memory()
-    sig_e = torch.empty(ns, 2 * cfg['n_steps'] + 1, dtype=torch.complex128, device='cuda')
-    x_e = torch.empty(ns, dtype=torch.float64, device='cuda')
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0.record(st)
-    for b in range(args.steps):
-        pl.phi.copy_(phi_h, non_blocking=True)
-        pl.run_batch(base + 500000 + b * ns, sig_e, x_e)
-        sig_h.copy_(sig_e, non_blocking=True)
-        x_h.copy_(x_e, non_blocking=True)
-        pl.qp(sig_e, x_e, eps_ks)           # returns host scalars (synchronises)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
-    ms_e2e = replicas.max_over_ranks(ms_e2e, dist, 'cuda')
-    e2e = dict(value=replicas.job_throughput(units_per_step(cfg), args.steps, world, ms_e2e), unit=UNIT,
-               h2d_bytes_per_step=phi_h.numel() * 4, d2h_bytes_per_step=sig_h.numel() * 16 + x_h.numel() * 8 + 32)
-    # plain FP32 form (Sigma reductions, transform and QP in FP32) on the same samples as the
-    # mixed form (FP64 there): the eV difference of the QP energy
-    prec = precision_comparison(cfg, pl, ks, base)
-    cvres = cv_study(args, cfg, pl, ks, base) if args.cv > 0 else None
-    # the metric's comparison: time to +-0.03 eV of the chosen form (mixed precision + control
-    # variate) and of the plain FP32 form (no control variate, FP32 reductions at their own speed)
-    chosen = None
-    if cvres is not None:
-        plain_s = cvres['time_to_0_03eV_plain_s'] * prec['ms_per_step_plain_fp32'] / prec['ms_per_step_mixed']
-        chosen = dict(plain_fp32_seconds=round(plain_s, 1), chosen_seconds=cvres['time_to_0_03eV_cv_s'],
-                      chosen_seconds_incl_training=cvres['time_to_0_03eV_cv_incl_training_s'],
-                      speedup=round(plain_s / cvres['time_to_0_03eV_cv_s'], 3),
-                      speedup_incl_training=round(plain_s / cvres['time_to_0_03eV_cv_incl_training_s'], 3))
-    split = split_study(cfg, pl)
-    xis = xi_study(args, cfg, sysd, ks, pl, base) if args.xi else None
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
-    rl = roofline(prof, peaks)
-    cpu = cpu_baseline_subprocess(args) if world == 1 and not args.no_cpu_baseline else None
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
-                ms_per_step=ms_per_step, higher_is_better=True, scaling='weak', vs_baseline=None, dtype='c64/f32 + f64',
-                data='synthetic',
-                config=dict(workload=cfg['workload'], n_cheb=cfg['n_cheb'], cheb_deg=cfg['cheb_deg'], dt=cfg['dt'],
-                            samples_per_step=ns * world, tdh_orbitals_per_launch=2 * cfg['n_eta'] * cfg['samples_per_batch'],
-                            zeta_vectors_per_launch=2 * ns,
-                            l2='inputs larger than L2 (about 20 GB live per step)',
-                            precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world,
-                            cuda_graphs=bool(args.graphs),
-                            launch_tuning=dict(zip(('plane_operand_prefetch', 'plane_lookahead', 'pencil_lookahead',
-                                                    'plane_variant'),
-                                                   pl.tuning)) if pl.tuning else 'defaults',
-                            roofline_timing='per-kernel CUDA events over the timed region' if not args.graphs else
-                            'per-kernel CUDA events over one extra step (graph replay is timed unprofiled)'),
-                e2e=e2e, gpu_launches=int(launches), roofline=rl, cpu_baseline=cpu,
-                clocks=clk, time_to_0_03eV=tt, time_to_0_03eV_chosen_vs_plain=chosen, precision_forms=prec,
-                control_variate=cvres, split_operator=split, xi_compression=xis,
-                setup=dict(seconds=round(t_setup, 2), e_homo=ks['e_homo'], e_lumo=ks['e_lumo'],
-                           gap_eV=round((ks['e_lumo'] - ks['e_homo']) * HA_EV, 4), emin=ks['emin'], emax=ks['emax'],
-                           eig_residual=float(ks['eig_residual'])))
-    print(json.dumps(line), flush=True)
+        sec = measure_whole_path(args, cfg, local, world, rank, dist, peaks, args.steps, args.warmup)
+        line = dict(metric=METRIC, value=sec['value'], unit=UNIT, n_gpus=world, steps=args.steps,
+                    warmup=args.warmup, ms_per_step=sec['ms_per_step'], higher_is_better=True, scaling='weak',
+                    vs_baseline=None, dtype='c64/f32 + f64', data='synthetic',
+                    config=dict(workload=cfg['workload'], parallelism='dp%d' % world), **{
+                        k: sec[k] for k in ('roofline', 'time_to_0_03eV', 'time_to_0_03eV_chosen_vs_plain',
+                                            'precision_forms', 'control_variate', 'setup')})
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline and 'step_time_steps' in cfg:
+            line['cpu_baseline'] = cpu_baseline_subprocess(args)
+        print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -500,8 +616,6 @@ def split_study(cfg, pl, seed=77):
             e1.record(st)
             e1.synchronize()
             out[name] = ng * B * steps * 3 / (e0.elapsed_time(e1) * 1e-3)
-        # accuracy on this system: the same vectors after 20 steps of each (Chebyshev-16 is exact to
-        # rounding at this dt, so the difference is the splitting error)
         a = torch.empty(8, ng, dtype=torch.complex64, device=pl.dev)
         pl.ctx.white_noise(seed + 1, 7, 0, 1, 8, a)
         b = a.clone()
@@ -517,11 +631,8 @@ def split_study(cfg, pl, seed=77):
 
 def xi_study(args, cfg, sysd, ks, pl, base, n_xi=10000, f_g=0.003, L=32):
     """The same samples through the full-grid pipeline and through one that carries u^R in the sparse
-    stochastic xi basis (n_xi functions of grid fraction f_g in segments of L points, the sizes of the
-    paper's runs), each timed with CUDA events after a warm-up run: time per step, bytes of the stored
-    u, and the spread the xi projection adds to the per-sample Re Sigma_i(eps_KS) against the Monte-Carlo
-    spread of the full-grid values."""
-    import numpy as np
+    stochastic xi basis, each timed with CUDA events after a warm-up run: time per step, bytes of the
+    stored u, and the spread the xi projection adds to the per-sample Re Sigma_i(eps_KS)."""
     import torch
     from paper_2601_21005_gb300.pipeline import Pipeline
     pxi = Pipeline(cfg['n'], cfg['h'], sysd['vloc'], sysd['kb_atoms'], ks['phi'], ks['e_homo'], ks['e_lumo'],
@@ -529,23 +640,19 @@ def xi_study(args, cfg, sysd, ks, pl, base, n_xi=10000, f_g=0.003, L=32):
                    n_cheb=cfg['n_cheb'], samples_per_batch=cfg['samples_per_batch'], seed=pl.seed, stream_id=1,
                    device=pl.dev.index, spectrum=(ks['emin'], ks['emax']), graphs=args.graphs,
                    zeta_group=cfg['zeta_group'], xi=dict(n_xi=n_xi, f_g=f_g, L=L))
-    if pl.tuning:
-        for key, v in enumerate(pl.tuning):
-            pxi.ctx.set_tuning(key, v)
     m = pl.run_samples
     N = cfg['n_steps']
     res = {}
     for name, p in (('full_grid', pl), ('xi', pxi)):
         sg = torch.empty(m, 2 * N + 1, dtype=torch.complex128, device='cuda')
         x = torch.empty(m, dtype=torch.float64, device='cuda')
-        p.run_batch(base + 700000, sg, x)                  # warm-up (graph capture)
+        p.run_batch(base + 700000, sg, x)
         st = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
         p.run_batch(base + 700000, sg, x)
         e1.record(st)
         e1.synchronize()
-        # per-sample Re Sigma_i(eps_KS) on the pipeline's stream (the context launches there)
         with p.on_stream():
             om = torch.tensor([ks['e_homo']], dtype=torch.float64, device='cuda')
             per = torch.empty(m, dtype=torch.complex128, device='cuda')
@@ -563,15 +670,16 @@ def xi_study(args, cfg, sysd, ks, pl, base, n_xi=10000, f_g=0.003, L=32):
                 qp_eV_full_grid=round(res['full_grid']['qp'] * HA_EV, 5), qp_eV_xi=round(res['xi']['qp'] * HA_EV, 5),
                 re_sigma_sd_eV_full_grid=round(sd_full * HA_EV, 5),
                 re_sigma_sd_eV_xi_minus_full=round(float(d.std(ddof=1)) * HA_EV, 5),
-                added_variance_ratio=round(float(d.var(ddof=1)) / max(sd_full ** 2, 1e-300), 4),
-                note='per-sample Re Sigma_i(eps_KS); the xi form is unbiased over the xi draws, so its added '
-                     'variance adds to the Monte-Carlo variance of the same samples')
+                added_variance_ratio=round(float(d.var(ddof=1)) / max(sd_full ** 2, 1e-300), 4))
 
 
-def cv_study(args, cfg, pl, ks, base):
-    """Train the control variate on args.cv plain samples, then time steps of the chosen form
-    (one batch of paired samples plus cheap samples per step) against the plain estimator on the
-    same paired samples."""
+def cv_study(args, cfg, pl, ks, base, plain_sample_s):
+    """Train the control variate on args.cv plain samples, then compare, at equal target error
+    (+-0.03 eV), the plain estimator charged its own per-sample time (plain_sample_s, the bench
+    step's time per sample) with the control-variate estimator charged for its paired samples
+    (the plain work plus their features) and for r = M/n cheap samples per paired one.  The
+    control variate's variance is that of its rows over n plus that of the cheap-sample mean over
+    M (the rows share that mean, so their spread cannot show it)."""
     import torch
     from paper_2601_21005_gb300.control_variate import ControlVariate
     ns = pl.run_samples
@@ -591,32 +699,47 @@ def cv_study(args, cfg, pl, ks, base):
         Y, F = cv.collect(ns, base + 400000 + b * ns)
         Ys.append(Y)
         Fs.append(F)
+    e1.record(st)
+    torch.cuda.synchronize()
+    n = ns * args.cv_paired_batches
+    paired_s = e0.elapsed_time(e1) * 1e-3 / n           # plain pipeline + the sample's features
+    e0.record(st)
     Fc = cv.cheap_features(n_cheap, base + 500000)
+    e1.record(st)
+    torch.cuda.synchronize()
+    cheap_s = e0.elapsed_time(e1) * 1e-3 / n_cheap
     Yp, Fp = torch.cat(Ys), torch.cat(Fs)
     S1, X1 = cv.rows(Fc, Fp, Yp)
     r_cv = pl.qp(S1, X1, ks['e_homo'])
-    e1.record(st)
-    torch.cuda.synchronize()
-    sec = e0.elapsed_time(e1) * 1e-3
+    Sc, Xc = cv.cheap_mean_rows(Fc, S1, X1)
+    r_cheap = pl.qp(Sc, Xc, ks['e_homo'])
     S0, X0 = cv.plain_rows(Yp)
     r_pl = pl.qp(S0, X0, ks['e_homo'])
     net_kept = cv.use_net
-    cv.use_net = False                    # the linear part alone, on the same rows
+    cv.use_net = False
     S2, X2 = cv.rows(Fc, Fp, Yp)
+    Sc2, Xc2 = cv.cheap_mean_rows(Fc, S2, X2)
     cv.use_net = net_kept
     r_lin = pl.qp(S2, X2, ks['e_homo'])
-    n = Yp.shape[0]
-    per_sample_s = sec / n                 # paired samples plus their share of the cheap ones
-    sd_pl, sd_cv = r_pl['se'] * HA_EV * n ** 0.5, r_cv['se'] * HA_EV * n ** 0.5
-    need_pl, need_cv = (sd_pl / 0.03) ** 2, (sd_cv / 0.03) ** 2
-    t_plain = need_pl * per_sample_s
-    t_cv = need_cv * per_sample_s
+    r_lin_c = pl.qp(Sc2, Xc2, ks['e_homo'])
+    se_cv = (r_cv['se'] ** 2 + r_cheap['se'] ** 2) ** 0.5
+    se_lin = (r_lin['se'] ** 2 + r_lin_c['se'] ** 2) ** 0.5
+    target = 0.03 / HA_EV
+    r = n_cheap / n
+    # per paired sample, the variance at ratio r: n se_rows^2 + (M se_cheap^2) / r
+    var_cv = n * r_cv['se'] ** 2 + n_cheap * r_cheap['se'] ** 2 / r
+    need_pl, need_cv = n * r_pl['se'] ** 2 / target ** 2, var_cv / target ** 2
+    t_plain = need_pl * plain_sample_s
+    t_cv = need_cv * (paired_s + r * cheap_s)
     return dict(n_train=args.cv, n_paired=n, n_cheap=n_cheap, train_seconds=round(t_train, 2),
                 heldout_loss_first_best=[round(va[0], 4), round(min(va), 4)] if va else None,
                 qp_eV_plain=round(r_pl['eps_qp'] * HA_EV, 5), se_eV_plain=round(r_pl['se'] * HA_EV, 5),
-                qp_eV_cv=round(r_cv['eps_qp'] * HA_EV, 5), se_eV_cv=round(r_cv['se'] * HA_EV, 5),
-                variance_gain=round((r_pl['se'] / r_cv['se']) ** 2, 3),
-                variance_gain_linear_part_alone=round((r_pl['se'] / r_lin['se']) ** 2, 3), network_kept=bool(net_kept),
+                qp_eV_cv=round(r_cv['eps_qp'] * HA_EV, 5), se_eV_cv=round(se_cv * HA_EV, 5),
+                se_eV_cv_rows=round(r_cv['se'] * HA_EV, 5), se_eV_cv_cheap_mean=round(r_cheap['se'] * HA_EV, 5),
+                variance_gain=round((r_pl['se'] / se_cv) ** 2, 3),
+                variance_gain_linear_part_alone=round((r_pl['se'] / se_lin) ** 2, 3), network_kept=bool(net_kept),
+                seconds_per_sample=dict(plain=round(plain_sample_s, 4), paired=round(paired_s, 4),
+                                        cheap=round(cheap_s, 6)),
                 time_to_0_03eV_plain_s=round(t_plain, 1), time_to_0_03eV_cv_s=round(t_cv, 1),
                 time_to_0_03eV_cv_incl_training_s=round(t_cv + t_train, 1),
                 speedup=round(t_plain / t_cv, 3), speedup_incl_training=round(t_plain / (t_cv + t_train), 3))
@@ -628,27 +751,38 @@ def main():
     ap.add_argument('--steps', type=int, default=5)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--config', default='si35h36_64', choices=sorted(CONFIGS))
+    ap.add_argument('--config', default='si7055h1596_288', choices=sorted(CONFIGS))
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--ks-cache', default=None,
-                    help='npz file for the Kohn-Sham inputs (read if present, else computed and written)')
+    ap.add_argument('--no-secondary', action='store_true', help='skip the 64^3 whole-path measurement')
+    ap.add_argument('--secondary-steps', type=int, default=3, help='timed steps of the 64^3 whole-path measurement')
     ap.add_argument('--no-graphs', dest='graphs', action='store_false',
                     help='launch every kernel directly instead of replaying the loops as CUDA graphs')
     ap.add_argument('--no-autotune', dest='autotune', action='store_false',
                     help='keep the default launch hints instead of timing the candidates at setup')
-    ap.add_argument('--no-xi', dest='xi', action='store_false', help='skip the xi-compression study')
+    ap.add_argument('--split-study', action='store_true', help='64^3: time the split-operator stepper as well')
+    ap.add_argument('--xi-study', action='store_true', help='64^3: time the xi-compressed pipeline as well')
     ap.add_argument('--cv', type=int, default=128, help='control-variate training samples (0: skip the study)')
     ap.add_argument('--cv-cheap', type=int, default=4096, help='cheap (features-only) samples in the study')
     ap.add_argument('--cv-paired-batches', type=int, default=8,
                     help='runs of paired samples in the study (8 runs of 16: 128 paired corrections)')
     ap.add_argument('--scale', type=float, default=1.0,
-                    help='scale N_tau and N_chb together (profiling captures of fewer launches)')
+                    help='64^3 / 16^3 configs: scale N_tau and N_chb together (profiling captures)')
+    ap.add_argument('--step-time-steps', type=int, default=None,
+                    help='288^3: time steps per bench step (smaller: profiling captures)')
+    ap.add_argument('--batch-samples', type=int, default=None,
+                    help='288^3: MC samples per batch (smaller: profiling captures)')
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
-    if args.scale != 1.0:
+    if args.scale != 1.0 and 'n_steps' in cfg:
         cfg['n_steps'] = max(2, int(round(cfg['n_steps'] * args.scale)))
         cfg['n_cheb'] = max(2, int(round(cfg['n_cheb'] * args.scale)))
         cfg['workload'] += ' (scaled: N_tau=%d, N_chb=%d)' % (cfg['n_steps'], cfg['n_cheb'])
+    if args.step_time_steps is not None and 'step_time_steps' in cfg:
+        cfg['step_time_steps'] = args.step_time_steps
+        cfg['workload'] += ' (reduced: %d time steps per step)' % args.step_time_steps
+    if args.batch_samples is not None and 'step_time_steps' in cfg:
+        cfg['samples_per_batch'] = args.batch_samples
+        cfg['workload'] += ' (reduced: %d samples per batch)' % args.batch_samples
     if args.impl == 'reference':
         run_reference(args, cfg)
     else:

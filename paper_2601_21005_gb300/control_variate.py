@@ -185,6 +185,21 @@ class ControlVariate:
         sig = t.view_as_complex(rows[:, :self.n_sig].contiguous().reshape(n, -1, 2)).contiguous()
         return sig, rows[:, self.n_sig].contiguous()
 
+    def cheap_mean_rows(self, F_cheap, sigma_rows, x_rows):
+        """Rows whose QP standard error is the part the paired rows cannot show: the spread of the
+        cheap-sample mean (1/M) sum_j f(x_j).  Every row z_i = mean_j f(x_j) + Y_i - f(x_i) shares
+        that mean, so its fluctuation is missing from the spread of the z_i; its variance is
+        Var_j f(x_j) / M.  The returned M rows are mean(z) + mean_j f(x_j) - f(x_k) (k over the cheap
+        samples): their mean is the estimate's, so the QP solve finds the same root and Z, and their
+        spread is that of f over the cheap samples.  Total standard error: the two added in
+        quadrature."""
+        with self.pl.on_stream():
+            t = self.torch
+            n = sigma_rows.shape[0]
+            z = t.cat([t.view_as_real(sigma_rows).reshape(n, -1), x_rows[:, None]], dim=1)
+            Y = z.mean(dim=0, keepdim=True).expand(F_cheap.shape[0], -1).contiguous()
+            return self._rows(F_cheap, F_cheap, Y)
+
     def plain_rows(self, Y_paired):
         n = Y_paired.shape[0]
         t = self.torch
