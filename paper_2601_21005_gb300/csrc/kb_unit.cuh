@@ -76,6 +76,7 @@ __device__ __forceinline__ void step_pointwise(const StepArgs& a, const VecInfo&
     const float2* bp = (dV != nullptr) ? a.b1 + (size_t)inf.partner * NG + uoff : nullptr;
     const float2 cpsi = a.coef.cpsi[inf.cset], ch = a.coef.ch[inf.cset], c2 = a.coef.c2[inf.cset];
     const float ebar = a.ebar, alpha = a.alpha;
+#pragma unroll 2
     for (int q = threadIdx.x; q < ROWS * N / 2; q += NT) {
         const int y = q / (N / 2), x = 2 * (q % (N / 2));
         const int o = y * N + x;

@@ -62,7 +62,7 @@ template <> struct CPlaneCfg<0> { static constexpr int W = 32; };
 template <> struct CPlaneCfg<1> { static constexpr int W = 18; };
 
 // ------------------------------------------------------------------ fused Chebyshev step
-// Cluster (8 CTAs) per plane z of vector b: grid (288 * 8, batch).  CTA c keeps the plane's columns
+// Cluster (8 CTAs) per plane z of vector b: grid (8 * batch, 288), vectors fastest in launch order.  CTA c keeps the plane's columns
 // 36c .. 36c + 35 in `colb` [y][36] and its rows 36c .. 36c + 35 in `rowb` [36][x].  Each transform
 // along x or y is a 288-point warp FFT of one line (warp_fft.cuh); warp w takes the lines
 // w, w + W, ... of the 36, loads a line, transforms it and stores it, so no transform waits at a
@@ -84,7 +84,7 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(CPlaneCfg<V>::W * 3
     float2* kcs = tws + CN;
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank();
-    const int z = blockIdx.x / CL, b = blockIdx.y;
+    const int b = blockIdx.x / CL, z = blockIdx.y;        // vectors fastest in launch order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n1 = wfft_n1(lane), k1 = wfft_k1(lane);
     const int u = z * CL + c;                              // KB unit: rows 36c .. 36c + 35 of plane z
@@ -174,68 +174,104 @@ __global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(CPlaneCfg<V>::W * 3
 // the potential and KB parts and the Chebyshev combine, and transforms back.  Four HBM passes per
 // term (with the z lines) instead of two, but every CTA is independent and two fit on an SM.
 constexpr int YT = 16;                  // x columns per y-line tile
+constexpr int YP = YT + 1;              // the shared-memory pitch of a warp-FFT tile
+constexpr int ZT_NT = 192;              // threads of a Stockham line tile of 16 columns
 constexpr int ROWS36_W = 12;            // warps of the row step (3 rows each)
-constexpr int YP = YT + 1;              // its shared-memory pitch
 
+// The y lines: tiles of 16 x-columns of one z plane, in place; radix plan 8, 4, 3, 3 with the first
+// stage loaded from HBM into registers and the last stage stored from registers (as the z lines).
 template <int DIR>
-__global__ void __launch_bounds__(YT * 32, 2) k_ylines288(float2* __restrict__ W, const float2* __restrict__ tw) {
-    constexpr int CNT = YT * 32;
+__global__ void __launch_bounds__(ZT_NT, 4) k_ylines288(float2* __restrict__ W, const float2* __restrict__ tw) {
+    constexpr int TX = YT, NT = ZT_NT;
     extern __shared__ __align__(16) float2 sm[];
-    float2* tws = sm + CN * YP;
-    for (int i = threadIdx.x; i < CN; i += CNT) tws[i] = __ldg(tw + i);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int xt = blockIdx.x % (CN / YT), z = blockIdx.x / (CN / YT);
-    float2* base = W + (size_t)blockIdx.y * CN * CN * CN + (size_t)z * CN * CN + xt * YT;
-    for (int q = threadIdx.x; q < CN * YT / 2; q += CNT) {
-        const int y = q / (YT / 2), x = 2 * (q % (YT / 2));
-        const float4 v = ld4(base + (size_t)y * CN + x);
-        sm[y * YP + x] = make_float2(v.x, v.y);
-        sm[y * YP + x + 1] = make_float2(v.z, v.w);
-    }
-    __syncthreads();
+    for (int i = threadIdx.x; i < CN; i += NT) sm[TX * CN + i] = __ldg(tw + i);
+    const TwShared tws{sm + TX * CN};
+    const int xt = blockIdx.x % (CN / TX), z = blockIdx.x / (CN / TX);
+    float2* base = W + (size_t)blockIdx.y * CN * CN * CN + (size_t)z * CN * CN + xt * TX;
     {
-        const int n1 = wfft_n1(lane), k1 = wfft_k1(lane);
-        float2 v[9];
+        constexpr int R = 8, NB = CN / R, TOT = TX * NB, PER = (TOT + NT - 1) / NT;
+        float2 v[PER][R];
 #pragma unroll
-        for (int n = 0; n < 9; ++n) v[n] = sm[(n1 + 32 * n) * YP + warp];
-        warp_fft288<DIR>(v, lane, tws);
+        for (int p = 0; p < PER; ++p) {
+            const int q = threadIdx.x + p * NT;
+            if (q < TOT) {
+                const int l = q % TX, j = q / TX;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) sm[(k + 9 * k1) * YP + warp] = v[k];
+                for (int r = 0; r < R; ++r) v[p][r] = __ldg(base + (size_t)(j + r * NB) * CN + l);
+            }
+        }
+        stage_r2s<CN, R, 1, TX, 1, TX, NT, DIR>(v, sm, tws);
     }
-    __syncthreads();
-    for (int q = threadIdx.x; q < CN * YT / 2; q += CNT) {
-        const int y = q / (YT / 2), x = 2 * (q % (YT / 2));
-        st4(base + (size_t)y * CN + x, sm[y * YP + x], sm[y * YP + x + 1]);
+    fft_stage<CN, 4, 8, TX, 1, TX, NT, DIR>(sm, tws);
+    fft_stage<CN, 3, 32, TX, 1, TX, NT, DIR>(sm, tws);
+    {
+        constexpr int R = 3, NS = 96, TOT = TX * NS, PER = (TOT + NT - 1) / NT;
+        float2 v[PER][R];
+        stage_s2r<CN, R, NS, TX, 1, TX, NT, DIR>(sm, v, tws);
+#pragma unroll
+        for (int p = 0; p < PER; ++p) {
+            const int q = threadIdx.x + p * NT;
+            if (q < TOT) {
+                const int l = q % TX, j = q / TX;
+#pragma unroll
+                for (int r = 0; r < R; ++r) base[(size_t)(j + r * NS) * CN + l] = v[p][r];
+            }
+        }
     }
 }
 
-// One CTA per 36-row unit u of vector b (after the inverse y lines): a warp loads each of its rows
-// straight from HBM, transforms it along x and stores it into shared memory; then the KB apply, the
-// pointwise step and the KB partials; then a warp transforms each row forward and writes it out.
+// One CTA per 36-row unit u of vector b (after the inverse y lines), vectors fastest in launch order:
+// the CTAs of one unit for all vectors run together, so the unit's potential rows and KB entries
+// come from DRAM once and from L2 for the other vectors (at 288^3 neither fits in L2 whole).  The
+// unit's rows are loaded with coalesced 16-byte loads, each row is transformed along x by a warp
+// FFT in place, then the KB apply, the pointwise step and the KB partials, then a warp transforms
+// each row forward and writes it out.  Thread 0 first asks L2 for the unit's pointwise operands
+// (b1, psi, b2, potential rows) so that they arrive while the transforms run.
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const float2* __restrict__ tw) {
     constexpr int CNT = NW * 32;
     constexpr size_t NG = (size_t)CN * CN * CN;
+    constexpr unsigned UB = CS * CN * sizeof(float2), VB = CS * CN * sizeof(float);
     extern __shared__ __align__(16) float2 sm[];
     float2* rowb = sm;
     float2* tws = rowb + CS * PR;
     float2* kcs = tws + CN;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n1 = wfft_n1(lane), k1 = wfft_k1(lane);
-    const int u = blockIdx.x, b = blockIdx.y;
+    const int b = blockIdx.x, u = blockIdx.y;
     const size_t uoff = (size_t)u * CS * CN;
     const size_t off = (size_t)b * NG + uoff;
-    for (int i = threadIdx.x; i < CN; i += CNT) tws[i] = __ldg(tw + i);
     const VecInfo inf = a.info[b];
+    if (threadIdx.x == 0) {
+        l2_prefetch(a.b1 + off, UB);
+        if (a.psi != nullptr) l2_prefetch(a.psi + off, UB);
+        if (a.b2 != nullptr) l2_prefetch(a.b2 + off, UB);
+        l2_prefetch(a.vpot + (size_t)inf.vrow * NG + uoff, VB);
+        if (a.dvpot != nullptr && inf.dvrow >= 0) {
+            l2_prefetch(a.dvpot + (size_t)inf.dvrow * NG + uoff, VB);
+            l2_prefetch(a.b1 + (size_t)inf.partner * NG + uoff, UB);
+        }
+    }
+    for (int i = threadIdx.x; i < CN; i += CNT) tws[i] = __ldg(tw + i);
     const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
     if (kc != nullptr) kb_stage_coeffs<CNT>(a, kc, u, kcs);
+    {
+        const float2* src = a.W + off;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < CS * CN / 2; q += CNT) {
+            const int y = q / (CN / 2), x = 2 * (q % (CN / 2));
+            const float4 v = ld4(src + y * CN + x);
+            rowb[y * PR + x] = make_float2(v.x, v.y);
+            rowb[y * PR + x + 1] = make_float2(v.z, v.w);
+        }
+    }
     __syncthreads();
     for (int l = warp; l < CS; l += NW) {
-        const float2* src = a.W + off + (size_t)l * CN;
         float2 v[9];
 #pragma unroll
-        for (int n = 0; n < 9; ++n) v[n] = __ldg(src + n1 + 32 * n);
+        for (int n = 0; n < 9; ++n) v[n] = rowb[l * PR + n1 + 32 * n];
         warp_fft288<+1>(v, lane, tws);
+        __syncwarp();
 #pragma unroll
         for (int k = 0; k < 9; ++k) rowb[l * PR + k + 9 * k1] = v[k];
     }
@@ -254,9 +290,15 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
         __syncwarp();
 #pragma unroll
         for (int k = 0; k < 9; ++k) rowb[l * PR + k + 9 * k1] = v[k];
-        __syncwarp();
-        float2* dst = a.Wout + off + (size_t)l * CN;
-        for (int q = lane; q < CN / 2; q += 32) st4(dst + 2 * q, rowb[l * PR + 2 * q], rowb[l * PR + 2 * q + 1]);
+    }
+    __syncthreads();
+    {
+        float2* dst = a.Wout + off;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < CS * CN / 2; q += CNT) {
+            const int y = q / (CN / 2), x = 2 * (q % (CN / 2));
+            st4(dst + y * CN + x, rowb[y * PR + x], rowb[y * PR + x + 1]);
+        }
     }
 }
 
@@ -386,7 +428,8 @@ __global__ void __launch_bounds__(YT * 32, 2) k_zlines_warp(float2* __restrict__
 template <int TX> static size_t zreg_smem() { return sizeof(float2) * ((size_t)TX * CN + CN); }
 
 static size_t rows36_smem(int max_unit_slots) { return sizeof(float2) * ((size_t)CS * PR + CN + 4 * (size_t)max_unit_slots); }
-static size_t ylines288_smem() { return sizeof(float2) * ((size_t)CN * YP + CN); }
+static size_t ylines288_smem() { return sizeof(float2) * ((size_t)CN * YT + CN); }
+static size_t zwarp_smem() { return sizeof(float2) * ((size_t)CN * YP + CN); }
 
 template <class K> static cudaError_t big_smem(K kern, size_t bytes) {
     cudaError_t e;
@@ -403,8 +446,8 @@ cudaError_t cluster_init_attributes(int max_unit_slots) {
     if ((e = big_smem(k_rows36_step<ROWS36_W>, rows36_smem(max_unit_slots)))) return e;
     if ((e = big_smem(k_ylines288<1>, ylines288_smem()))) return e;
     if ((e = big_smem(k_ylines288<-1>, ylines288_smem()))) return e;
-    if ((e = big_smem(k_zlines_warp<0>, ylines288_smem()))) return e;
-    if ((e = big_smem(k_zlines_warp<1>, ylines288_smem()))) return e;
+    if ((e = big_smem(k_zlines_warp<0>, zwarp_smem()))) return e;
+    if ((e = big_smem(k_zlines_warp<1>, zwarp_smem()))) return e;
     if ((e = cudaFuncSetAttribute(k_zlines_reg<16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zreg_smem<16>())))
         return e;
     if ((e = cudaFuncSetAttribute(k_zlines_reg<16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zreg_smem<16>())))
@@ -432,7 +475,7 @@ int cplane_blocks_per_sm(int variant, int max_unit_slots) {
 int zlines_reg_blocks_per_sm(int form) {
     int r = 0;
     if (form == 2)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_zlines_warp<0>, YT * 32, ylines288_smem());
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_zlines_warp<0>, YT * 32, zwarp_smem());
     else if (form == 1)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_zlines_reg<32, 0>, ZCfg<32>::NT, zreg_smem<32>());
     else
@@ -444,14 +487,14 @@ void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st
     if (batch == 0) return;
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     if (variant == 1) {
-        k_cplane_step<0><<<dim3(CN * CL, batch), CPlaneCfg<0>::W * 32, cplane_smem(slots), st>>>(a, tw);
+        k_cplane_step<0><<<dim3(CL * batch, CN), CPlaneCfg<0>::W * 32, cplane_smem(slots), st>>>(a, tw);
     } else if (variant == 2) {
-        k_cplane_step<1><<<dim3(CN * CL, batch), CPlaneCfg<1>::W * 32, cplane_smem(slots), st>>>(a, tw);
+        k_cplane_step<1><<<dim3(CL * batch, CN), CPlaneCfg<1>::W * 32, cplane_smem(slots), st>>>(a, tw);
     } else {
         const dim3 yg((CN / YT) * CN, batch);
-        k_ylines288<1><<<yg, YT * 32, ylines288_smem(), st>>>(const_cast<float2*>(a.W), tw);
-        k_rows36_step<ROWS36_W><<<dim3(CN * CL, batch), ROWS36_W * 32, rows36_smem(slots), st>>>(a, tw);
-        if (a.Wout != nullptr) k_ylines288<-1><<<yg, YT * 32, ylines288_smem(), st>>>(a.Wout, tw);
+        k_ylines288<1><<<yg, ZT_NT, ylines288_smem(), st>>>(const_cast<float2*>(a.W), tw);
+        k_rows36_step<ROWS36_W><<<dim3(batch, CN * CL), ROWS36_W * 32, rows36_smem(slots), st>>>(a, tw);
+        if (a.Wout != nullptr) k_ylines288<-1><<<yg, ZT_NT, ylines288_smem(), st>>>(a.Wout, tw);
     }
 }
 
@@ -461,9 +504,9 @@ void zlines_reg(float2* W, int batch, int kind, int form, float kscale, float ec
     if (form == 2) {
         const dim3 grid((CN / YT) * CN, batch);
         if (kind == 0)
-            k_zlines_warp<0><<<grid, YT * 32, ylines288_smem(), st>>>(W, kscale, ecut, tw);
+            k_zlines_warp<0><<<grid, YT * 32, zwarp_smem(), st>>>(W, kscale, ecut, tw);
         else
-            k_zlines_warp<1><<<grid, YT * 32, ylines288_smem(), st>>>(W, kscale, ecut, tw);
+            k_zlines_warp<1><<<grid, YT * 32, zwarp_smem(), st>>>(W, kscale, ecut, tw);
     } else if (form == 1) {
         const dim3 grid((CN / 32) * CN, batch);
         if (kind == 0)

@@ -189,8 +189,8 @@ def states_near_gap(ctx, n_occ, emin, emax, m=16, sigma=None, n_probe=16, count_
     """E_HOMO, E_LUMO and the HOMO orbital of an n_occ-occupied system without computing every
     occupied state.  Returns (e_homo, e_lumo, phi_homo [N_g] real float64 normalised to
     dV sum phi^2 = 1, info): info holds the gap centre, the estimated state count there and its
-    standard error, the Ritz values and residuals.  When the HOMO level is degenerate, phi_homo is
-    one vector of that level.  ctx needs max_batch >= max(m, n_probe).  log: optional callable
+    standard error, the Ritz values and residuals, and the LUMO orbital (phi_lumo, same normalisation).
+    When the HOMO or LUMO level is degenerate, the orbital is one vector of that level.  ctx needs max_batch >= max(m, n_probe).  log: optional callable
     taking a progress line (the gap search, then each iteration's HOMO/LUMO Ritz values).
 
     The window is the Jackson-damped Gaussian of degree window_degree; its default width sigma is
@@ -251,12 +251,13 @@ def states_near_gap(ctx, n_occ, emin, emax, m=16, sigma=None, n_probe=16, count_
     ih, il = pair(w)
     if ih is None or il is None:
         raise RuntimeError('no Ritz value on one side of the gap centre')
-    q = Q[ih].cpu().numpy().astype(np.complex128)
-    k = np.argmax(np.abs(q))
-    r = (q * np.exp(-1j * np.angle(q[k]))).real
-    r /= np.sqrt(ctx.dV * np.sum(r * r))
-    if r.sum() < 0:
-        r = -r
+    def real_orbital(i):
+        q = Q[i].cpu().numpy().astype(np.complex128)
+        k = np.argmax(np.abs(q))
+        r = (q * np.exp(-1j * np.angle(q[k]))).real
+        r /= np.sqrt(ctx.dV * np.sum(r * r))
+        return -r if r.sum() < 0 else r
+
     info = dict(gap_centre=ef, count_at_gap=n_ef, count_se=se_ef, ritz=w.tolist(), residuals=res.tolist(),
-                max_residual=float(max(res[ih], res[il])))
-    return float(w[ih]), float(w[il]), r, info
+                max_residual=float(max(res[ih], res[il])), phi_lumo=real_orbital(il))
+    return float(w[ih]), float(w[il]), real_orbital(ih), info
