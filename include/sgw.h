@@ -111,8 +111,8 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
  *                               first and last stages in registers (default), 1 = the same with 32
  *                               columns, 2 = tiles of 16 columns with one warp FFT per column
  * On row-path grids (n = 48, 96, 288) the other keys are accepted and have no effect, and the
- * autotuner keeps their current values; SGW_TUNE_PLANE_VARIANT and SGW_TUNE_LINE_FORM act at
- * n = 288.
+ * autotuner keeps their current values; SGW_TUNE_PLANE_VARIANT, SGW_TUNE_LINE_FORM and
+ * SGW_TUNE_PLANE_OPERANDS (for the row form's 36-row step) act at n = 288.
  * sgw_set_tuning returns SGW_EINVAL for an unknown key or a negative value (a value above 1 for
  * SGW_TUNE_PLANE_OPERANDS, above 2 for SGW_TUNE_PLANE_VARIANT or SGW_TUNE_LINE_FORM) and drops the context's cached graphs; sgw_get_tuning writes the current
  * value to *value_host.
@@ -515,7 +515,9 @@ enum {
     SGW_PROF_TIME_ORDER = 6,   /* time ordering                                            */
     SGW_PROF_OTHER = 7,        /* everything else                                          */
     SGW_PROF_SPLIT_INV = 8,    /* inverse plane pass of a split-operator step              */
-    SGW_PROF_KINDS = 9
+    SGW_PROF_LINES = 9,        /* y-line passes of the 288 grid's row form (16 bytes per
+                                  vector-point each); the 36-row step is SGW_PROF_PLANE_STEP  */
+    SGW_PROF_KINDS = 10
 };
 
 /* enable != 0: from now on record CUDA events on the context's stream around every kernel

@@ -400,9 +400,28 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
             const double per = 8.0 * (2 + (a.psi ? 1 : 0) + (a.b2 ? 1 : 0) + 1 + (a.Wout ? 1 : 0));
             double bytes = per * (double)ctx->ng * batch + 4.0 * (double)ctx->ng * vrows * (dvpot ? 2 : 1);
             if (a.kbc) bytes += 4.0 * (double)ctx->ng + 20.0 * (double)ctx->kb.n_sup;
-            Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
-            sgw::launch_plane_step(n, a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_PLANE_VARIANT]);
-            CKL();
+            if (sgw::cluster_plane(n) && ctx->tune[SGW_TUNE_PLANE_VARIANT] == 0) {
+                // the row form of the 288 grid: y lines, 36-row step, y lines, each timed on its own
+                {
+                    Launch Ly(ctx, SGW_PROF_LINES, 1, 16.0 * (double)ctx->ng * batch);
+                    sgw::lines288(ctx->W, batch, +1, ctx->tw, st);
+                    CKL();
+                }
+                {
+                    Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
+                    sgw::rows36_step(a, batch, ctx->tw, st);
+                    CKL();
+                }
+                if (a.Wout != nullptr) {
+                    Launch Ly(ctx, SGW_PROF_LINES, 1, 16.0 * (double)ctx->ng * batch);
+                    sgw::lines288(a.Wout, batch, -1, ctx->tw, st);
+                    CKL();
+                }
+            } else {
+                Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
+                sgw::launch_plane_step(n, a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_PLANE_VARIANT]);
+                CKL();
+            }
         }
     }
     return SGW_OK;
@@ -815,6 +834,7 @@ sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
         if (key == SGW_TUNE_LINE_FORM) cand = sgw::cluster_plane(ctx->n) ? std::vector<int>{0, 1, 2}
                                                                           : std::vector<int>{ctx->tune[key]};
         else if (key == SGW_TUNE_PLANE_VARIANT && sgw::cluster_plane(ctx->n)) cand = {0, 1, 2};
+        else if (key == SGW_TUNE_PLANE_OPERANDS && sgw::cluster_plane(ctx->n)) cand = {0, 1};
         else if (sgw::rows_path(ctx->n)) cand = {ctx->tune[key]};   // the row kernels take no other launch hints
         int best_v = 0;
         float best = 1e30f;

@@ -67,7 +67,7 @@ __device__ __forceinline__ void kb_project_unit(const StepArgs& a, int u, int b,
 // The pointwise part of the fused step on ROWS x N unit points starting at global offset `off`
 // (vector b's unit; sm holds H_kin b1 + V_NL b1 at pitch P): out = cpsi psi + ch alpha (h + (V - Ebar) b1
 // [+ dv b1_partner]) + c2 b2, written to global memory and back into sm.
-template <int N, int ROWS, int P, int NT>
+template <int N, int ROWS, int P, int NT, int UNROLL = 2>
 __device__ __forceinline__ void step_pointwise(const StepArgs& a, const VecInfo& inf, size_t off, size_t uoff,
                                                float2* sm) {
     constexpr size_t NG = (size_t)N * N * N;
@@ -76,7 +76,7 @@ __device__ __forceinline__ void step_pointwise(const StepArgs& a, const VecInfo&
     const float2* bp = (dV != nullptr) ? a.b1 + (size_t)inf.partner * NG + uoff : nullptr;
     const float2 cpsi = a.coef.cpsi[inf.cset], ch = a.coef.ch[inf.cset], c2 = a.coef.c2[inf.cset];
     const float ebar = a.ebar, alpha = a.alpha;
-#pragma unroll 2
+#pragma unroll UNROLL
     for (int q = threadIdx.x; q < ROWS * N / 2; q += NT) {
         const int y = q / (N / 2), x = 2 * (q % (N / 2));
         const int o = y * N + x;

@@ -223,10 +223,18 @@ __global__ void __launch_bounds__(ZT_NT, 4) k_ylines288(float2* __restrict__ W, 
 // One CTA per 36-row unit u of vector b (after the inverse y lines), vectors fastest in launch order:
 // the CTAs of one unit for all vectors run together, so the unit's potential rows and KB entries
 // come from DRAM once and from L2 for the other vectors (at 288^3 neither fits in L2 whole).  The
-// unit's rows are loaded with coalesced 16-byte loads, each row is transformed along x by a warp
-// FFT in place, then the KB apply, the pointwise step and the KB partials, then a warp transforms
-// each row forward and writes it out.  Thread 0 first asks L2 for the unit's pointwise operands
-// (b1, psi, b2, potential rows) so that they arrive while the transforms run.
+// unit's rows are copied into shared memory by 16-byte cp.async copies (all in flight at once, no
+// registers held), each row is transformed along x by a warp FFT in place, then the KB apply, the
+// pointwise step and the KB partials, then a warp transforms each row forward and the rows are
+// written out.  With a.pf_operands thread 0 first asks L2 for the unit's pointwise operands (b1, psi,
+// b2, potential rows) so that they arrive while the transforms run (a launch hint).
+constexpr int PR36 = CN + 2;            // row pitch of the 36-row step: rows start on 16-byte boundaries
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const float2* __restrict__ tw) {
     constexpr int CNT = NW * 32;
@@ -234,7 +242,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
     constexpr unsigned UB = CS * CN * sizeof(float2), VB = CS * CN * sizeof(float);
     extern __shared__ __align__(16) float2 sm[];
     float2* rowb = sm;
-    float2* tws = rowb + CS * PR;
+    float2* tws = rowb + CS * PR36;
     float2* kcs = tws + CN;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n1 = wfft_n1(lane), k1 = wfft_k1(lane);
@@ -242,7 +250,15 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
     const size_t uoff = (size_t)u * CS * CN;
     const size_t off = (size_t)b * NG + uoff;
     const VecInfo inf = a.info[b];
-    if (threadIdx.x == 0) {
+    {
+        const float2* src = a.W + off;
+        for (int q = threadIdx.x; q < CS * CN / 2; q += CNT) {
+            const int y = q / (CN / 2), x = 2 * (q % (CN / 2));
+            cp_async16(rowb + y * PR36 + x, src + y * CN + x);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    if (a.pf_operands && threadIdx.x == 0) {
         l2_prefetch(a.b1 + off, UB);
         if (a.psi != nullptr) l2_prefetch(a.psi + off, UB);
         if (a.b2 != nullptr) l2_prefetch(a.b2 + off, UB);
@@ -255,41 +271,32 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
     for (int i = threadIdx.x; i < CN; i += CNT) tws[i] = __ldg(tw + i);
     const float2* kc = a.kbc != nullptr ? a.kbc + (size_t)b * a.n_proj : nullptr;
     if (kc != nullptr) kb_stage_coeffs<CNT>(a, kc, u, kcs);
-    {
-        const float2* src = a.W + off;
-#pragma unroll 4
-        for (int q = threadIdx.x; q < CS * CN / 2; q += CNT) {
-            const int y = q / (CN / 2), x = 2 * (q % (CN / 2));
-            const float4 v = ld4(src + y * CN + x);
-            rowb[y * PR + x] = make_float2(v.x, v.y);
-            rowb[y * PR + x + 1] = make_float2(v.z, v.w);
-        }
-    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     for (int l = warp; l < CS; l += NW) {
         float2 v[9];
 #pragma unroll
-        for (int n = 0; n < 9; ++n) v[n] = rowb[l * PR + n1 + 32 * n];
+        for (int n = 0; n < 9; ++n) v[n] = rowb[l * PR36 + n1 + 32 * n];
         warp_fft288<+1>(v, lane, tws);
         __syncwarp();
 #pragma unroll
-        for (int k = 0; k < 9; ++k) rowb[l * PR + k + 9 * k1] = v[k];
+        for (int k = 0; k < 9; ++k) rowb[l * PR36 + k + 9 * k1] = v[k];
     }
     __syncthreads();
-    if (kc != nullptr) kb_apply_unit<CN, PR, CNT>(a, u, kcs, rowb);
-    step_pointwise<CN, CS, PR, CNT>(a, inf, off, uoff, rowb);
+    if (kc != nullptr) kb_apply_unit<CN, PR36, CNT>(a, u, kcs, rowb);
+    step_pointwise<CN, CS, PR36, CNT, 4>(a, inf, off, uoff, rowb);
     if (a.Wout == nullptr) return;
     __syncthreads();
-    if (a.kbp != nullptr) kb_project_unit<CN, PR, CNT>(a, u, b, rowb);
+    if (a.kbp != nullptr) kb_project_unit<CN, PR36, CNT>(a, u, b, rowb);
     __syncthreads();
     for (int l = warp; l < CS; l += NW) {
         float2 v[9];
 #pragma unroll
-        for (int n = 0; n < 9; ++n) v[n] = rowb[l * PR + n1 + 32 * n];
+        for (int n = 0; n < 9; ++n) v[n] = rowb[l * PR36 + n1 + 32 * n];
         warp_fft288<-1>(v, lane, tws);
         __syncwarp();
 #pragma unroll
-        for (int k = 0; k < 9; ++k) rowb[l * PR + k + 9 * k1] = v[k];
+        for (int k = 0; k < 9; ++k) rowb[l * PR36 + k + 9 * k1] = v[k];
     }
     __syncthreads();
     {
@@ -297,7 +304,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
 #pragma unroll 4
         for (int q = threadIdx.x; q < CS * CN / 2; q += CNT) {
             const int y = q / (CN / 2), x = 2 * (q % (CN / 2));
-            st4(dst + y * CN + x, rowb[y * PR + x], rowb[y * PR + x + 1]);
+            st4(dst + y * CN + x, rowb[y * PR36 + x], rowb[y * PR36 + x + 1]);
         }
     }
 }
@@ -427,7 +434,7 @@ __global__ void __launch_bounds__(YT * 32, 2) k_zlines_warp(float2* __restrict__
 // ------------------------------------------------------------------ launchers
 template <int TX> static size_t zreg_smem() { return sizeof(float2) * ((size_t)TX * CN + CN); }
 
-static size_t rows36_smem(int max_unit_slots) { return sizeof(float2) * ((size_t)CS * PR + CN + 4 * (size_t)max_unit_slots); }
+static size_t rows36_smem(int max_unit_slots) { return sizeof(float2) * ((size_t)CS * PR36 + CN + 4 * (size_t)max_unit_slots); }
 static size_t ylines288_smem() { return sizeof(float2) * ((size_t)CN * YT + CN); }
 static size_t zwarp_smem() { return sizeof(float2) * ((size_t)CN * YP + CN); }
 
@@ -491,11 +498,25 @@ void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st
     } else if (variant == 2) {
         k_cplane_step<1><<<dim3(CL * batch, CN), CPlaneCfg<1>::W * 32, cplane_smem(slots), st>>>(a, tw);
     } else {
-        const dim3 yg((CN / YT) * CN, batch);
-        k_ylines288<1><<<yg, ZT_NT, ylines288_smem(), st>>>(const_cast<float2*>(a.W), tw);
-        k_rows36_step<ROWS36_W><<<dim3(batch, CN * CL), ROWS36_W * 32, rows36_smem(slots), st>>>(a, tw);
-        if (a.Wout != nullptr) k_ylines288<-1><<<yg, ZT_NT, ylines288_smem(), st>>>(a.Wout, tw);
+        lines288(const_cast<float2*>(a.W), batch, +1, tw, st);
+        rows36_step(a, batch, tw, st);
+        if (a.Wout != nullptr) lines288(a.Wout, batch, -1, tw, st);
     }
+}
+
+void lines288(float2* W, int batch, int dir, const float2* tw, cudaStream_t st) {
+    if (batch == 0) return;
+    const dim3 yg((CN / YT) * CN, batch);
+    if (dir > 0)
+        k_ylines288<1><<<yg, ZT_NT, ylines288_smem(), st>>>(W, tw);
+    else
+        k_ylines288<-1><<<yg, ZT_NT, ylines288_smem(), st>>>(W, tw);
+}
+
+void rows36_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st) {
+    if (batch == 0) return;
+    const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
+    k_rows36_step<ROWS36_W><<<dim3(batch, CN * CL), ROWS36_W * 32, rows36_smem(slots), st>>>(a, tw);
 }
 
 // form 0: register-ended Stockham tiles of 16 columns, 1: of 32 columns, 2: warp-FFT tiles of 16

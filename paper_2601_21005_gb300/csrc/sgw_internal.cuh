@@ -165,6 +165,10 @@ int zlines_reg_blocks_per_sm(int form);
 void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant);
 // form 0 / 1: register-ended Stockham tiles of 16 / 32 columns, 2: warp-FFT tiles of 16 columns
 void zlines_reg(float2* W, int batch, int kind, int form, float kscale, float ecut, const float2* tw, cudaStream_t st);
+// the row form's passes one by one (the library times them separately): y lines in place on W
+// (dir +1 inverse, -1 forward) and the 36-row step
+void lines288(float2* W, int batch, int dir, const float2* tw, cudaStream_t st);
+void rows36_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st);
 
 // ---- other kernels (kernels_misc.cu)
 void launch_noise(int ng, uint64_t seed, uint32_t stream_id, int sample0, int n_samples, int n_vec,

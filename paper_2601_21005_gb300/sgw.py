@@ -15,7 +15,7 @@ from . import build as _build
 _lib = None
 
 PROF_KINDS = ['plane_step', 'pencil', 'kb_project', 'plane_fwd', 'tdh_density', 'sigma', 'time_order', 'other',
-              'split_inv']
+              'split_inv', 'lines']
 
 SGW_STATUS = {0: 'SGW_OK', 1: 'SGW_EINVAL', 2: 'SGW_ENOMEM', 3: 'SGW_ECUDA', 4: 'SGW_ESTATE',
               5: 'SGW_ETIMEOUT', 6: 'SGW_ENOCONV'}

@@ -178,14 +178,17 @@ def test_propagate_parity(cluster32):
     h = lambda v: ham.apply_h(v, g, s['vloc'], kb)
     xd = gc.to_dev(x.reshape(B, -1), torch, torch.complex64)
     ref = x.astype(np.complex64).astype(np.complex128)
-    for nsteps, tol in ((1, 1e-5), (19, 2e-5 * 20)):
+    # the stated bar, 1e-5 relative per step, after 1 and after 20 steps in all
+    for nsteps, total in ((1, 1), (19, 20)):
         c.propagate(xd, nsteps, 0.05, 16, dirs)
         for b in range(B):
             for _ in range(nsteps):
                 ref[b] = cheb.propagate_step(h, ref[b], lo, hi, 0.05 * dirs[b], 16)
         got = xd.cpu().numpy().reshape(ref.shape)
+        errs = [gc.rel_err(got[b], ref[b]) for b in range(B)]
+        print('propagation after %d steps: largest relative error %.2e (bar %.1e)' % (total, max(errs), 1e-5 * total))
         for b in range(B):
-            assert gc.rel_err(got[b], ref[b]) < tol, (nsteps, b)
+            assert errs[b] < 1e-5 * total, (total, b)
             # unitary in FP32
             assert abs(np.linalg.norm(got[b]) - np.linalg.norm(ref[b])) < 1e-5 * np.linalg.norm(ref[b])
 
