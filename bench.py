@@ -42,16 +42,17 @@ CONFIGS = {
     # the large cluster: the largest configuration that fits one GPU
     'si7055h1596_288': dict(
         system='si_cluster', n=288, h=0.5, radius=61.0, samples_per_batch=4, zeta_group=1, n_eta=8,
-        step_time_steps=4, n_tau=1000, dt=0.05, cheb_deg=16, n_cheb=4000, xi=dict(n_xi=10000, f_g=0.003, L=32),
-        # occupied-filter window: centred on the gap the kernel-polynomial search finds for this
-        # cluster (-0.0895 Ha, count 14907.6 +- 42 at n_occ = 14908); the target orbital is a
-        # stand-in (a normalised Gaussian at the cluster centre): the cost of a step does not
-        # depend on either
+        step_time_steps=4, n_tau=1000, dt=0.05, cheb_deg=16, n_cheb=7000, xi=dict(n_xi=10000, f_g=0.003, L=32),
+        # occupied-filter window: the gap of this cluster in its kernel-polynomial density of states
+        # at degree 8000 (below 20 states/Ha from -0.105 to -0.075 Ha, centre -0.0895 Ha, count
+        # 14910.0 +- 42 at n_occ = 14908), and a filter degree for a gap of ~0.03 Ha; the target
+        # orbital is a stand-in (a normalised Gaussian at the cluster centre): the cost of a step
+        # does not depend on it
         e_homo=-0.1045, e_lumo=-0.0745,
         workload='Si7055H1596 cluster, 288^3 grid h=0.5 bohr, 29816 electrons, KB on 7055 Si; one batch of '
                  '4 MC samples = 64 TDH orbitals (8 eta pairs each) + 8 zeta vectors, xi-compressed u '
                  '(N_xi=10000, f_g=0.003, L=32), Chebyshev degree 16, dt=0.05; per step 4 TDH + 4 zeta time '
-                 'steps with Sigma(t) and the QP solve after the batch\'s occupied filter (degree 4000, at setup)'),
+                 'steps with Sigma(t) and the QP solve after the batch\'s occupied filter (degree 7000, at setup)'),
     # the small cluster, whole path per step
     'si35h36_64': dict(system='si_cluster', n=64, h=0.5, radius=10.5, samples_per_batch=4, zeta_group=4, n_eta=8,
                        n_steps=400, dt=0.05, cheb_deg=16, n_cheb=2000, workload='Si35H36 cluster, 64^3 grid '
@@ -333,7 +334,8 @@ def measure_large(args, cfg, local, world, rank, dist, peaks):
     kctx.close()
     seed = 1000 * 5
     base = replicas.sample_base(rank)
-    pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs, n_steps=S, xi=cfg['xi'])
+    pl = make_pipeline(cfg, sysd, ks, local, seed, graphs=args.graphs, autotune=args.autotune, n_steps=S,
+                       xi=cfg['xi'])
     del sysd
     ns = step_samples(cfg)
     st = torch.cuda.current_stream()
@@ -412,9 +414,11 @@ def measure_large(args, cfg, local, world, rank, dist, peaks):
     rl = roofline(prof, peaks, n)
     peak_gb = round(torch.cuda.max_memory_allocated(local) / 1e9, 1)
     pl.ctx.close()
+    tuning = dict(zip(('plane_operand_prefetch', 'plane_lookahead', 'pencil_lookahead', 'plane_variant',
+                       'line_form'), pl.tuning)) if pl.tuning else 'defaults'
     return dict(value=value, ms=ms, ms_per_step=ms / args.steps, launches=launches, clocks=clk, e2e=e2e,
                 roofline=rl, filter=filt, setup_seconds=round(t_setup, 1), peak_device_gb=peak_gb,
-                spectrum=[pl.emin, pl.emax])
+                spectrum=[pl.emin, pl.emax], tuning=tuning)
 
 
 # ---------------------------------------------------------------- our arm: the 64^3 whole path
@@ -466,12 +470,12 @@ def measure_whole_path(args, cfg, local, world, rank, dist, peaks, steps, warmup
     if cvres is not None:
         # the chosen form (mixed precision + control variate) against the plain FP32 form (no control
         # variate, FP32 reductions at their own measured speed)
-        plain_s = cvres['time_to_0_03eV_plain_s'] * prec['ms_per_step_plain_fp32'] / prec['ms_per_step_mixed']
+        plain_s = cvres['time_to_target_plain_s'] * prec['ms_per_step_plain_fp32'] / prec['ms_per_step_mixed']
         chosen = dict(workload=cfg['workload'], plain_fp32_seconds=round(plain_s, 1),
-                      chosen_seconds=cvres['time_to_0_03eV_cv_s'],
-                      chosen_seconds_incl_training=cvres['time_to_0_03eV_cv_incl_training_s'],
-                      speedup=round(plain_s / cvres['time_to_0_03eV_cv_s'], 3),
-                      speedup_incl_training=round(plain_s / cvres['time_to_0_03eV_cv_incl_training_s'], 3))
+                      chosen_seconds=cvres['time_to_target_cv_s'],
+                      chosen_seconds_incl_training=cvres['time_to_target_cv_incl_training_s'],
+                      speedup=round(plain_s / cvres['time_to_target_cv_s'], 3),
+                      speedup_incl_training=round(plain_s / cvres['time_to_target_cv_incl_training_s'], 3))
     out = dict(workload=cfg['workload'], value=value, unit=UNIT, ms_per_step=round(ms_per_step, 1), steps=steps,
                warmup=warmup, roofline=roofline(prof, peaks, cfg['n']), time_to_0_03eV=tt,
                time_to_0_03eV_chosen_vs_plain=chosen, precision_forms=prec, control_variate=cvres,
@@ -516,7 +520,7 @@ def run_ours(args, cfg):
                                 zeta_vectors_per_launch=2 * step_samples(cfg), xi=cfg['xi'],
                                 l2='inputs larger than L2 (the 64 TDH orbitals alone are 12 GB)',
                                 precision='FP32 propagation, FP64 Sigma/transform/QP', parallelism='dp%d' % world,
-                                cuda_graphs=bool(args.graphs),
+                                cuda_graphs=bool(args.graphs), launch_tuning=big['tuning'],
                                 roofline_timing='per-kernel CUDA events over one extra step with direct launches '
                                                 '(graph replay is timed unprofiled)'),
                     e2e=big['e2e'], gpu_launches=int(big['launches']), roofline=big['roofline'], cpu_baseline=None,
@@ -674,75 +678,9 @@ def xi_study(args, cfg, sysd, ks, pl, base, n_xi=10000, f_g=0.003, L=32):
 
 
 def cv_study(args, cfg, pl, ks, base, plain_sample_s):
-    """Train the control variate on args.cv plain samples, then compare, at equal target error
-    (+-0.03 eV), the plain estimator charged its own per-sample time (plain_sample_s, the bench
-    step's time per sample) with the control-variate estimator charged for its paired samples
-    (the plain work plus their features) and for r = M/n cheap samples per paired one.  The
-    control variate's variance is that of its rows over n plus that of the cheap-sample mean over
-    M (the rows share that mean, so their spread cannot show it)."""
-    import torch
-    from paper_2601_21005_gb300.control_variate import ControlVariate
-    ns = pl.run_samples
-    cv = ControlVariate(pl, m2max=10, width=256, max_batch=256, seed=11)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    Yt, Ft = cv.collect(args.cv, base + 300000)
-    tr, va = cv.train(Ft, Yt, epochs=200, batch=64, lr=1e-3)
-    torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
-    n_cheap = args.cv_cheap
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    Ys, Fs = [], []
-    e0.record(st)
-    for b in range(args.cv_paired_batches):
-        Y, F = cv.collect(ns, base + 400000 + b * ns)
-        Ys.append(Y)
-        Fs.append(F)
-    e1.record(st)
-    torch.cuda.synchronize()
-    n = ns * args.cv_paired_batches
-    paired_s = e0.elapsed_time(e1) * 1e-3 / n           # plain pipeline + the sample's features
-    e0.record(st)
-    Fc = cv.cheap_features(n_cheap, base + 500000)
-    e1.record(st)
-    torch.cuda.synchronize()
-    cheap_s = e0.elapsed_time(e1) * 1e-3 / n_cheap
-    Yp, Fp = torch.cat(Ys), torch.cat(Fs)
-    S1, X1 = cv.rows(Fc, Fp, Yp)
-    r_cv = pl.qp(S1, X1, ks['e_homo'])
-    Sc, Xc = cv.cheap_mean_rows(Fc, S1, X1)
-    r_cheap = pl.qp(Sc, Xc, ks['e_homo'])
-    S0, X0 = cv.plain_rows(Yp)
-    r_pl = pl.qp(S0, X0, ks['e_homo'])
-    net_kept = cv.use_net
-    cv.use_net = False
-    S2, X2 = cv.rows(Fc, Fp, Yp)
-    Sc2, Xc2 = cv.cheap_mean_rows(Fc, S2, X2)
-    cv.use_net = net_kept
-    r_lin = pl.qp(S2, X2, ks['e_homo'])
-    r_lin_c = pl.qp(Sc2, Xc2, ks['e_homo'])
-    se_cv = (r_cv['se'] ** 2 + r_cheap['se'] ** 2) ** 0.5
-    se_lin = (r_lin['se'] ** 2 + r_lin_c['se'] ** 2) ** 0.5
-    target = 0.03 / HA_EV
-    r = n_cheap / n
-    # per paired sample, the variance at ratio r: n se_rows^2 + (M se_cheap^2) / r
-    var_cv = n * r_cv['se'] ** 2 + n_cheap * r_cheap['se'] ** 2 / r
-    need_pl, need_cv = n * r_pl['se'] ** 2 / target ** 2, var_cv / target ** 2
-    t_plain = need_pl * plain_sample_s
-    t_cv = need_cv * (paired_s + r * cheap_s)
-    return dict(n_train=args.cv, n_paired=n, n_cheap=n_cheap, train_seconds=round(t_train, 2),
-                heldout_loss_first_best=[round(va[0], 4), round(min(va), 4)] if va else None,
-                qp_eV_plain=round(r_pl['eps_qp'] * HA_EV, 5), se_eV_plain=round(r_pl['se'] * HA_EV, 5),
-                qp_eV_cv=round(r_cv['eps_qp'] * HA_EV, 5), se_eV_cv=round(se_cv * HA_EV, 5),
-                se_eV_cv_rows=round(r_cv['se'] * HA_EV, 5), se_eV_cv_cheap_mean=round(r_cheap['se'] * HA_EV, 5),
-                variance_gain=round((r_pl['se'] / se_cv) ** 2, 3),
-                variance_gain_linear_part_alone=round((r_pl['se'] / se_lin) ** 2, 3), network_kept=bool(net_kept),
-                seconds_per_sample=dict(plain=round(plain_sample_s, 4), paired=round(paired_s, 4),
-                                        cheap=round(cheap_s, 6)),
-                time_to_0_03eV_plain_s=round(t_plain, 1), time_to_0_03eV_cv_s=round(t_cv, 1),
-                time_to_0_03eV_cv_incl_training_s=round(t_cv + t_train, 1),
-                speedup=round(t_plain / t_cv, 3), speedup_incl_training=round(t_plain / (t_cv + t_train), 3))
+    """The control variate against the plain estimator at equal target error (control_variate.study)."""
+    from paper_2601_21005_gb300.control_variate import study
+    return study(pl, ks['e_homo'], args.cv, args.cv_paired_batches, args.cv_cheap, base, plain_sample_s)
 
 
 def main():
@@ -771,6 +709,8 @@ def main():
                     help='288^3: time steps per bench step (smaller: profiling captures)')
     ap.add_argument('--batch-samples', type=int, default=None,
                     help='288^3: MC samples per batch (smaller: profiling captures)')
+    ap.add_argument('--n-cheb', type=int, default=None,
+                    help='288^3: degree of the occupied filter at setup (smaller: profiling captures)')
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
     if args.scale != 1.0 and 'n_steps' in cfg:
@@ -780,6 +720,9 @@ def main():
     if args.step_time_steps is not None and 'step_time_steps' in cfg:
         cfg['step_time_steps'] = args.step_time_steps
         cfg['workload'] += ' (reduced: %d time steps per step)' % args.step_time_steps
+    if args.n_cheb is not None and 'step_time_steps' in cfg:
+        cfg['n_cheb'] = args.n_cheb
+        cfg['workload'] += ' (reduced: filter degree %d)' % args.n_cheb
     if args.batch_samples is not None and 'step_time_steps' in cfg:
         cfg['samples_per_batch'] = args.batch_samples
         cfg['workload'] += ' (reduced: %d samples per batch)' % args.batch_samples

@@ -18,9 +18,13 @@ The steps:
             z_i = mean_j f(x_j) + Y_i - f(x_i) (FP64) and solve the QP equation on them.  The
             estimate is unbiased for any f; with no cheap samples it is the plain one.
 """
+import time
+
 import numpy as np
 
 from . import sgw as _sgw
+
+HA_EV = 27.211386245988
 
 
 class ControlVariate:
@@ -205,3 +209,74 @@ class ControlVariate:
         t = self.torch
         return (t.view_as_complex(Y_paired[:, :self.n_sig].contiguous().reshape(n, -1, 2)).contiguous(),
                 Y_paired[:, self.n_sig].contiguous())
+
+
+def study(pl, eps_ks, n_train, paired_batches, n_cheap, sample0, plain_sample_s, target_ev=0.03, epochs=200):
+    """Train the control variate on n_train plain samples, then compare, at equal target error
+    (target_ev on the QP energy), the plain estimator charged its own per-sample time
+    (plain_sample_s) with the control-variate estimator charged for its paired samples (the plain
+    work plus their features) and for r = M/n cheap samples per paired one.  The control variate's
+    variance is that of its rows over n plus that of the cheap-sample mean over M (the rows share
+    that mean, so their spread cannot show it).  Samples: training from sample0 + 300000, paired
+    from sample0 + 400000, cheap from sample0 + 500000.  Returns a dict of the measured figures."""
+    import torch
+    ns = pl.run_samples
+    cv = ControlVariate(pl, m2max=10, width=256, max_batch=256, seed=11)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Yt, Ft = cv.collect(n_train, sample0 + 300000)
+    tr, va = cv.train(Ft, Yt, epochs=epochs, batch=64, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    Ys, Fs = [], []
+    e0.record(st)
+    for b in range(paired_batches):
+        Y, F = cv.collect(ns, sample0 + 400000 + b * ns)
+        Ys.append(Y)
+        Fs.append(F)
+    e1.record(st)
+    torch.cuda.synchronize()
+    n = ns * paired_batches
+    paired_s = e0.elapsed_time(e1) * 1e-3 / n           # plain pipeline + the sample's features
+    e0.record(st)
+    Fc = cv.cheap_features(n_cheap, sample0 + 500000)
+    e1.record(st)
+    torch.cuda.synchronize()
+    cheap_s = e0.elapsed_time(e1) * 1e-3 / n_cheap
+    Yp, Fp = torch.cat(Ys), torch.cat(Fs)
+    S1, X1 = cv.rows(Fc, Fp, Yp)
+    r_cv = pl.qp(S1, X1, eps_ks)
+    Sc, Xc = cv.cheap_mean_rows(Fc, S1, X1)
+    r_cheap = pl.qp(Sc, Xc, eps_ks)
+    S0, X0 = cv.plain_rows(Yp)
+    r_pl = pl.qp(S0, X0, eps_ks)
+    net_kept = cv.use_net
+    cv.use_net = False
+    S2, X2 = cv.rows(Fc, Fp, Yp)
+    Sc2, Xc2 = cv.cheap_mean_rows(Fc, S2, X2)
+    cv.use_net = net_kept
+    r_lin = pl.qp(S2, X2, eps_ks)
+    r_lin_c = pl.qp(Sc2, Xc2, eps_ks)
+    se_cv = (r_cv['se'] ** 2 + r_cheap['se'] ** 2) ** 0.5
+    se_lin = (r_lin['se'] ** 2 + r_lin_c['se'] ** 2) ** 0.5
+    target = target_ev / HA_EV
+    r = n_cheap / n
+    # per paired sample, the variance at ratio r: n se_rows^2 + (M se_cheap^2) / r
+    var_cv = n * r_cv['se'] ** 2 + n_cheap * r_cheap['se'] ** 2 / r
+    need_pl, need_cv = n * r_pl['se'] ** 2 / target ** 2, var_cv / target ** 2
+    t_plain = need_pl * plain_sample_s
+    t_cv = need_cv * (paired_s + r * cheap_s)
+    return dict(n_train=n_train, n_paired=n, n_cheap=n_cheap, train_seconds=round(t_train, 2),
+                heldout_loss_first_best=[round(va[0], 4), round(min(va), 4)] if va else None,
+                qp_eV_plain=round(r_pl['eps_qp'] * HA_EV, 5), se_eV_plain=round(r_pl['se'] * HA_EV, 5),
+                qp_eV_cv=round(r_cv['eps_qp'] * HA_EV, 5), se_eV_cv=round(se_cv * HA_EV, 5),
+                se_eV_cv_rows=round(r_cv['se'] * HA_EV, 5), se_eV_cv_cheap_mean=round(r_cheap['se'] * HA_EV, 5),
+                variance_gain=round((r_pl['se'] / se_cv) ** 2, 3),
+                variance_gain_linear_part_alone=round((r_pl['se'] / se_lin) ** 2, 3), network_kept=bool(net_kept),
+                seconds_per_sample=dict(plain=round(plain_sample_s, 4), paired=round(paired_s, 4),
+                                        cheap=round(cheap_s, 6)),
+                time_to_target_plain_s=round(t_plain, 1), time_to_target_cv_s=round(t_cv, 1),
+                time_to_target_cv_incl_training_s=round(t_cv + t_train, 1), target_eV=target_ev,
+                speedup=round(t_plain / t_cv, 3), speedup_incl_training=round(t_plain / (t_cv + t_train), 3))
