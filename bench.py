@@ -207,6 +207,18 @@ def roofline(prof, peaks, n):
                 other_kernels_gbs={k: round(x['alg_bytes'] / (x['ms'] * 1e-3) / 1e9, 1) for k, x in kinds.items()})
 
 
+def nvtx_range(torch, name):
+    """Open (name) or close (None) an NVTX push/pop range around the timed steps, so that a
+    profiler's launch list can be limited to them (`ncu --nvtx --nvtx-include timed_steps/`)."""
+    try:
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
 def time_to_target(pl, sig, xs, eps_ks, seconds_per_sample, target_ev=0.03):
     """Samples needed for a QP standard error of target_ev, from the per-sample spread so far."""
     r = pl.qp(sig, xs, eps_ks)
@@ -368,10 +380,12 @@ def measure_large(args, cfg, local, world, rank, dist, peaks):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    nvtx_range(torch, 'timed_steps')
     e0.record(st)
     for _ in range(args.steps):
         step()
     e1.record(st)
+    nvtx_range(torch, None)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()

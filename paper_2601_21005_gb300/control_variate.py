@@ -30,7 +30,7 @@ HA_EV = 27.211386245988
 class ControlVariate:
     # ridge 0.1 (on standardised inputs): the best held-out variance ratio of the linear part for
     # 128 and 256 training samples on the 64^3 cluster (2.52 / 2.69 against 2.42 / 2.66 at 1e-3)
-    def __init__(self, pipeline, m2max=10, width=256, seed=77, max_batch=256, ridge=0.1):
+    def __init__(self, pipeline, m2max=10, width=256, seed=77, max_batch=256, ridge=0.1, linear=True):
         import torch
         self.torch = torch
         self.pl = pipeline
@@ -41,6 +41,7 @@ class ControlVariate:
         self.n_out = self.n_sig + 1
         self.max_batch = max_batch
         self.ridge = ridge
+        self.linear = linear        # False: no linear part (f_lin = 0), the network alone on Y
         self.lin = torch.zeros(_sgw.sgw_cv_linear_size(self.n_feat, self.n_out), dtype=torch.float64,
                                device=pipeline.dev)
         self.use_net = True
@@ -115,11 +116,12 @@ class ControlVariate:
         n = F.shape[0]
         nv = max(1, int(round(holdout * n))) if n > 4 else 0
         ntr = n - nv
-        Fs = self._shells(F)
-        ctx.cv_linear_fit(Fs[:ntr].contiguous(), Y[:ntr].contiguous(), self.ridge, self.lin)
-        R = t.empty_like(Y)
-        ctx.cv_linear_apply(self.lin, Fs, self.n_out, R, y=Y)         # residuals Y - f_lin(x)
-        Y = R
+        if self.linear:
+            Fs = self._shells(F)
+            ctx.cv_linear_fit(Fs[:ntr].contiguous(), Y[:ntr].contiguous(), self.ridge, self.lin)
+            R = t.empty_like(Y)
+            ctx.cv_linear_apply(self.lin, Fs, self.n_out, R, y=Y)     # residuals Y - f_lin(x)
+            Y = R
         Fs = F.clone()
         ctx.cv_standardize_f32(Fs[:ntr], self.mu_x, self.sd_x, True)
         if nv:
@@ -256,11 +258,30 @@ def study(pl, eps_ks, n_train, paired_batches, n_cheap, sample0, plain_sample_s,
     cv.use_net = False
     S2, X2 = cv.rows(Fc, Fp, Yp)
     Sc2, Xc2 = cv.cheap_mean_rows(Fc, S2, X2)
-    cv.use_net = net_kept
     r_lin = pl.qp(S2, X2, eps_ks)
     r_lin_c = pl.qp(Sc2, Xc2, eps_ks)
+    # the linear part with the network on its residual whether or not the hold-out test kept it
+    cv.use_net = True
+    S4, X4 = cv.rows(Fc, Fp, Yp)
+    Sc4, Xc4 = cv.cheap_mean_rows(Fc, S4, X4)
+    r_both, r_both_c = pl.qp(S4, X4, eps_ks), pl.qp(Sc4, Xc4, eps_ks)
+    cv.use_net = net_kept
+    # the network alone (no linear part), trained on the same samples and used as trained
+    t1 = time.perf_counter()
+    cvn = ControlVariate(pl, m2max=10, width=256, max_batch=256, seed=11, linear=False)
+    cvn.train(Ft, Yt, epochs=epochs, batch=64, lr=1e-3)
+    net_alone_kept = cvn.use_net
+    cvn.use_net = True
+    S3, X3 = cvn.rows(Fc, Fp, Yp)
+    Sc3, Xc3 = cvn.cheap_mean_rows(Fc, S3, X3)
+    r_net, r_net_c = pl.qp(S3, X3, eps_ks), pl.qp(Sc3, Xc3, eps_ks)
+    cvn.mlp.close()
+    torch.cuda.synchronize()
+    t_net_alone = time.perf_counter() - t1
     se_cv = (r_cv['se'] ** 2 + r_cheap['se'] ** 2) ** 0.5
     se_lin = (r_lin['se'] ** 2 + r_lin_c['se'] ** 2) ** 0.5
+    se_both = (r_both['se'] ** 2 + r_both_c['se'] ** 2) ** 0.5
+    se_net = (r_net['se'] ** 2 + r_net_c['se'] ** 2) ** 0.5
     target = target_ev / HA_EV
     r = n_cheap / n
     # per paired sample, the variance at ratio r: n se_rows^2 + (M se_cheap^2) / r
@@ -275,6 +296,9 @@ def study(pl, eps_ks, n_train, paired_batches, n_cheap, sample0, plain_sample_s,
                 se_eV_cv_rows=round(r_cv['se'] * HA_EV, 5), se_eV_cv_cheap_mean=round(r_cheap['se'] * HA_EV, 5),
                 variance_gain=round((r_pl['se'] / se_cv) ** 2, 3),
                 variance_gain_linear_part_alone=round((r_pl['se'] / se_lin) ** 2, 3), network_kept=bool(net_kept),
+                variance_gain_linear_plus_network=round((r_pl['se'] / se_both) ** 2, 3),
+                variance_gain_network_alone=round((r_pl['se'] / se_net) ** 2, 3),
+                network_alone_passed_holdout=bool(net_alone_kept), network_alone_train_seconds=round(t_net_alone, 2),
                 seconds_per_sample=dict(plain=round(plain_sample_s, 4), paired=round(paired_s, 4),
                                         cheap=round(cheap_s, 6)),
                 time_to_target_plain_s=round(t_plain, 1), time_to_target_cv_s=round(t_cv, 1),
