@@ -69,6 +69,10 @@ CONFIGS = {
 # only while that source is unchanged.
 TRAFFIC = {
     ('plane_step', 64): dict(ratio=839.2 / 806.4, source='kernels_grid.cu', sha='', capture='64-vector launch'),
+    # k_rows36_step, third term of a 4-vector kernel_bench step: 5.815 GB read + written against
+    # 4.998 GB algorithmic
+    ('plane_step', 288): dict(ratio=5.815 / 4.998, sha='864355dd4e601b8c', capture='4-vector launch',
+                              source=('kernels_cluster.cu', 'kb_unit.cuh', 'warp_fft.cuh')),
 }
 
 
@@ -81,9 +85,13 @@ def load_peaks():
     return dict(hbm_gbs=6800.0, bf16_tflops=1900.0, source='fallback')
 
 
-def source_sha(name):
-    with open(os.path.join(ROOT, 'paper_2601_21005_gb300', 'csrc', name), 'rb') as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def source_sha(names):
+    """sha256 prefix of the concatenated kernel sources (a file name or a tuple of them)."""
+    h = hashlib.sha256()
+    for name in ((names,) if isinstance(names, str) else names):
+        with open(os.path.join(ROOT, 'paper_2601_21005_gb300', 'csrc', name), 'rb') as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 class ClockSampler:
@@ -197,7 +205,8 @@ def roofline(prof, peaks, n):
     if tr is not None and tr['sha'] and tr['sha'] == source_sha(tr['source']):
         traffic = round(tr['ratio'] * v['alg_bytes'] / v['launches'])
         tsrc = ('ncu dram__bytes_read.sum + dram__bytes_write.sum of a %s of this kernel source (%s %s), '
-                'scaled by algorithmic bytes to the average launch' % (tr['capture'], tr['source'], tr['sha']))
+                'scaled by algorithmic bytes to the average launch' % (tr['capture'], '+'.join(
+                    (tr['source'],) if isinstance(tr['source'], str) else tr['source']), tr['sha']))
     return dict(bound='hbm', achieved=round(gbs, 1), peak=peak, unit='GB/s', frac=round(gbs / peak, 4),
                 traffic=traffic, traffic_source=tsrc, kernel=name, launches=v['launches'],
                 avg_launch_us=round(1e3 * v['ms'] / v['launches'], 2), alg_bytes_per_launch=round(v['alg_bytes'] /
