@@ -106,15 +106,20 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
  *                               as 0); at n = 288: 0 = row form (passes over y lines and over
  *                               36-row units, default), 1 = one thread-block cluster of 8 CTAs
  *                               per xy plane with 32 warps per CTA, 2 = the same with 18 warps
- *   SGW_TUNE_LINE_FORM        : form of the z-line pass on the 288 grid: 0 = tiles of 16
- *                               kx-columns transformed by radix stages in shared memory with the
+ *   SGW_TUNE_LINE_FORM        : form of the line passes on the 288 grid: 0 = z lines on tiles of
+ *                               16 kx-columns transformed by radix stages in shared memory with the
  *                               first and last stages in registers (default), 1 = the same with 32
- *                               columns, 2 = tiles of 16 columns with one warp FFT per column
+ *                               columns, 2 = tiles of 16 columns with one warp FFT per column;
+ *                               3 = the z lines and the row form's y lines by a two-stage
+ *                               16 x 18 transform (one shared-memory round trip per transform),
+ *                               4 = form 3 with the 36-row step's rows transformed the same way
+ *                               instead of by warp FFTs.  Forms 0-2 leave the y lines on radix
+ *                               stages.
  * On row-path grids (n = 48, 96, 288) the other keys are accepted and have no effect, and the
  * autotuner keeps their current values; SGW_TUNE_PLANE_VARIANT, SGW_TUNE_LINE_FORM and
  * SGW_TUNE_PLANE_OPERANDS (for the row form's 36-row step) act at n = 288.
  * sgw_set_tuning returns SGW_EINVAL for an unknown key or a negative value (a value above 1 for
- * SGW_TUNE_PLANE_OPERANDS, above 2 for SGW_TUNE_PLANE_VARIANT or SGW_TUNE_LINE_FORM) and drops the context's cached graphs; sgw_get_tuning writes the current
+ * SGW_TUNE_PLANE_OPERANDS, above 2 for SGW_TUNE_PLANE_VARIANT, above 4 for SGW_TUNE_LINE_FORM) and drops the context's cached graphs; sgw_get_tuning writes the current
  * value to *value_host.
  */
 enum {
@@ -132,7 +137,7 @@ sgw_status sgw_get_tuning(sgw_ctx* ctx, int key, int* value_host);
  * Autotuner: time `reps` degree-8 Chebyshev sums (the propagator's two-pass term, KB included when
  * a KB part is set) on a scratch batch of `batch` vectors for each candidate value (plane-pass
  * variant 0/1/2, then operand prefetch 0/1, then the lookaheads 0 and 1/2, 1, 3/2, 2 waves of resident
- * blocks from the occupancy of this GPU, then the z-line form 0/1/2 at n = 288), keep the fastest per key, each key timed with the
+ * blocks from the occupancy of this GPU, then the line form 0-4 at n = 288), keep the fastest per key, each key timed with the
  * choices already made for the keys before it, and write the chosen values to chosen_host
  * [SGW_TUNE_KEYS] (may be NULL).  Needs sgw_set_potential and a spectral interval (SGW_ESTATE
  * otherwise); 1 <= batch <= max_batch and reps >= 1 (SGW_EINVAL otherwise).  Uses a context work

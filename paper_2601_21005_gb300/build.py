@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, 'csrc')
 OUT = os.path.join(HERE, '_build')
 LIB = os.path.join(OUT, 'libsgw.so')
-SOURCES = ['kernels_grid.cu', 'kernels_rows.cu', 'kernels_cluster.cu', 'kernels_misc.cu', 'kernels_mlp.cu', 'abi.cu']
+SOURCES = ['kernels_grid.cu', 'kernels_rows.cu', 'kernels_cluster.cu', 'kernels_lines288.cu', 'kernels_misc.cu',
+           'kernels_mlp.cu', 'abi.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '--expt-relaxed-constexpr']
 

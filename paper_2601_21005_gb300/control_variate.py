@@ -242,6 +242,8 @@ def study(pl, eps_ks, n_train, paired_batches, n_cheap, sample0, plain_sample_s,
     torch.cuda.synchronize()
     n = ns * paired_batches
     paired_s = e0.elapsed_time(e1) * 1e-3 / n           # plain pipeline + the sample's features
+    if plain_sample_s is None:                           # the plain form charged the paired time
+        plain_sample_s = paired_s
     e0.record(st)
     Fc = cv.cheap_features(n_cheap, sample0 + 500000)
     e1.record(st)

@@ -404,22 +404,23 @@ sgw_status run_series(sgw_ctx* ctx, const std::vector<Step>& plan, const float2*
                 // the row form of the 288 grid: y lines, 36-row step, y lines, each timed on its own
                 {
                     Launch Ly(ctx, SGW_PROF_LINES, 1, 16.0 * (double)ctx->ng * batch);
-                    sgw::lines288(ctx->W, batch, +1, ctx->tw, st);
+                    sgw::lines288(ctx->W, batch, +1, ctx->tune[SGW_TUNE_LINE_FORM], ctx->tw, st);
                     CKL();
                 }
                 {
                     Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
-                    sgw::rows36_step(a, batch, ctx->tw, st);
+                    sgw::rows36_step(a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_LINE_FORM]);
                     CKL();
                 }
                 if (a.Wout != nullptr) {
                     Launch Ly(ctx, SGW_PROF_LINES, 1, 16.0 * (double)ctx->ng * batch);
-                    sgw::lines288(a.Wout, batch, -1, ctx->tw, st);
+                    sgw::lines288(a.Wout, batch, -1, ctx->tune[SGW_TUNE_LINE_FORM], ctx->tw, st);
                     CKL();
                 }
             } else {
                 Launch L(ctx, SGW_PROF_PLANE_STEP, 1, bytes);
-                sgw::launch_plane_step(n, a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_PLANE_VARIANT]);
+                sgw::launch_plane_step(n, a, batch, ctx->tw, st, ctx->tune[SGW_TUNE_PLANE_VARIANT],
+                                       ctx->tune[SGW_TUNE_LINE_FORM]);
                 CKL();
             }
         }
@@ -762,7 +763,7 @@ sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value) {
     if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
     if (key < 0 || key >= SGW_TUNE_KEYS) return fail(ctx, SGW_EINVAL, "unknown tuning key");
     if (value < 0 || (key == SGW_TUNE_PLANE_OPERANDS && value > 1) || (key == SGW_TUNE_PLANE_VARIANT && value > 2) ||
-        (key == SGW_TUNE_LINE_FORM && value > 2))
+        (key == SGW_TUNE_LINE_FORM && value > 4))
         return fail(ctx, SGW_EINVAL, "tuning value out of range");
     clear_graphs(ctx);
     ctx->tune[key] = value;
@@ -831,7 +832,7 @@ sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
             const int R = per_sm * nsm;
             cand = {0, R / 2, R, (3 * R) / 2, 2 * R};
         }
-        if (key == SGW_TUNE_LINE_FORM) cand = sgw::cluster_plane(ctx->n) ? std::vector<int>{0, 1, 2}
+        if (key == SGW_TUNE_LINE_FORM) cand = sgw::cluster_plane(ctx->n) ? std::vector<int>{0, 1, 2, 3, 4}
                                                                           : std::vector<int>{ctx->tune[key]};
         else if (key == SGW_TUNE_PLANE_VARIANT && sgw::cluster_plane(ctx->n)) cand = {0, 1, 2};
         else if (key == SGW_TUNE_PLANE_OPERANDS && sgw::cluster_plane(ctx->n)) cand = {0, 1};
@@ -1084,7 +1085,8 @@ sgw_status sgw_apply_h(sgw_ctx* ctx, const void* in_dev, void* out_dev, int batc
     }
     {
         Launch L(ctx, SGW_PROF_PLANE_STEP);
-        sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream, ctx->tune[SGW_TUNE_PLANE_VARIANT]);
+        sgw::launch_plane_step(ctx->n, a, batch, ctx->tw, ctx->stream, ctx->tune[SGW_TUNE_PLANE_VARIANT],
+                               ctx->tune[SGW_TUNE_LINE_FORM]);
         CKL();
     }
     return SGW_OK;

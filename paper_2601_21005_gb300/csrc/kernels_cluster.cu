@@ -461,7 +461,10 @@ cudaError_t cluster_init_attributes(int max_unit_slots) {
         return e;
     if ((e = cudaFuncSetAttribute(k_zlines_reg<32, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zreg_smem<32>())))
         return e;
-    return cudaFuncSetAttribute(k_zlines_reg<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zreg_smem<32>());
+    if ((e = cudaFuncSetAttribute(k_zlines_reg<32, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zreg_smem<32>())))
+        return e;
+    if ((e = rows36_2s_init_attributes(max_unit_slots))) return e;
+    return lines288_2s_init_attributes();
 }
 
 // variant 0: the row form; 1, 2: the cluster form with 32 / 18 warps
@@ -481,6 +484,7 @@ int cplane_blocks_per_sm(int variant, int max_unit_slots) {
 
 int zlines_reg_blocks_per_sm(int form) {
     int r = 0;
+    if (form >= 3) return lines288_2s_blocks_per_sm();
     if (form == 2)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, k_zlines_warp<0>, YT * 32, zwarp_smem());
     else if (form == 1)
@@ -490,7 +494,7 @@ int zlines_reg_blocks_per_sm(int form) {
     return r;
 }
 
-void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
+void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant, int line_form) {
     if (batch == 0) return;
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     if (variant == 1) {
@@ -498,14 +502,15 @@ void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st
     } else if (variant == 2) {
         k_cplane_step<1><<<dim3(CL * batch, CN), CPlaneCfg<1>::W * 32, cplane_smem(slots), st>>>(a, tw);
     } else {
-        lines288(const_cast<float2*>(a.W), batch, +1, tw, st);
-        rows36_step(a, batch, tw, st);
-        if (a.Wout != nullptr) lines288(a.Wout, batch, -1, tw, st);
+        lines288(const_cast<float2*>(a.W), batch, +1, line_form, tw, st);
+        rows36_step(a, batch, tw, st, line_form);
+        if (a.Wout != nullptr) lines288(a.Wout, batch, -1, line_form, tw, st);
     }
 }
 
-void lines288(float2* W, int batch, int dir, const float2* tw, cudaStream_t st) {
+void lines288(float2* W, int batch, int dir, int form, const float2* tw, cudaStream_t st) {
     if (batch == 0) return;
+    if (form >= 3) return ylines288_2s(W, batch, dir, tw, st);
     const dim3 yg((CN / YT) * CN, batch);
     if (dir > 0)
         k_ylines288<1><<<yg, ZT_NT, ylines288_smem(), st>>>(W, tw);
@@ -513,16 +518,20 @@ void lines288(float2* W, int batch, int dir, const float2* tw, cudaStream_t st) 
         k_ylines288<-1><<<yg, ZT_NT, ylines288_smem(), st>>>(W, tw);
 }
 
-void rows36_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st) {
+void rows36_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int form) {
     if (batch == 0) return;
+    if (form == 4) return rows36_2s_step(a, batch, tw, st);
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     k_rows36_step<ROWS36_W><<<dim3(batch, CN * CL), ROWS36_W * 32, rows36_smem(slots), st>>>(a, tw);
 }
 
-// form 0: register-ended Stockham tiles of 16 columns, 1: of 32 columns, 2: warp-FFT tiles of 16
+// form 0: register-ended Stockham tiles of 16 columns, 1: of 32 columns, 2: warp-FFT tiles of 16,
+// 3, 4: two-stage 16 x 18 tiles of 16
 void zlines_reg(float2* W, int batch, int kind, int form, float kscale, float ecut, const float2* tw, cudaStream_t st) {
     if (batch == 0) return;
-    if (form == 2) {
+    if (form >= 3) {
+        zlines288_2s(W, batch, kind, kscale, ecut, tw, st);
+    } else if (form == 2) {
         const dim3 grid((CN / YT) * CN, batch);
         if (kind == 0)
             k_zlines_warp<0><<<grid, YT * 32, zwarp_smem(), st>>>(W, kscale, ecut, tw);

@@ -965,8 +965,9 @@ void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, fl
     });
 }
 
-void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
-    if (rows_path(n)) return rows_plane_step(n, a, batch, tw, st, variant);
+void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant,
+                       int line_form) {
+    if (rows_path(n)) return rows_plane_step(n, a, batch, tw, st, variant, line_form);
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     const size_t sm = plane_step_smem(n, slots);
     if (variant == 2 && !plane_pipe_supported(n)) variant = 0;

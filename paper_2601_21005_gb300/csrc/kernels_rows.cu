@@ -368,9 +368,9 @@ void rows_zlines_energy(int n, const float2* W, int batch, float kscale, const f
 
 // The W input of the step is transformed back along y in place (the plane path leaves it intact;
 // every caller overwrites W afterwards).  At 288 one cluster of CTAs per plane does the whole pass.
-void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant) {
+void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant, int line_form) {
     if (batch == 0) return;
-    if (cluster_plane(n)) return cplane_step(a, batch, tw, st, variant);
+    if (cluster_plane(n)) return cplane_step(a, batch, tw, st, variant, line_form);
     ylines(n, const_cast<float2*>(a.W), batch, +1, tw, st);
     const int slots = a.kbc != nullptr ? a.max_plane_slots : 0;
     SGW_DISPATCH_ROWS(n, k_rows_step<N><<<dim3(N * N / RR, batch), RNT, rows_step_smem(N, slots), st>>>(a, tw));

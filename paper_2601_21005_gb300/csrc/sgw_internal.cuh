@@ -115,7 +115,8 @@ void launch_kb_split(const int* atoms, int n_atoms_colour, const KBDev& kb, cons
 int pencil_blocks(int n);
 void launch_pencil_coulomb_energy(int n, const float2* W, int batch, int per, float kscale, double dvn,
                                   const float2* tw, double* part, double* acc, cudaStream_t st);
-void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant = 0);
+void launch_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant = 0,
+                       int line_form = 0);
 // inverse xy transform of W (in place along y on the row path; W is scratch), epilogue:
 // mode 0 -> out_c[b] = plane (c64);
 // mode 1 (Poisson of TDH densities) -> vtot[b] = vloc + Re, dv[b] = Im, uR[b] = Im (if uR)
@@ -146,7 +147,8 @@ void rows_pencil(int n, float2* W, int batch, int kind, float kscale, float ecut
                  int line_form);
 void rows_zlines_energy(int n, const float2* W, int batch, float kscale, const float2* tw, double* part,
                         cudaStream_t st);
-void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant);
+void rows_plane_step(int n, const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant,
+                     int line_form = 0);
 void rows_plane_inv(int n, const float2* W, int batch, const float2* tw, int mode, float2* out_c, const float* vloc,
                     float* vtot, float* dv, float* uR, int64_t uR_stride, float* out_re, cudaStream_t st);
 void rows_density_fwd(int n, const float2* psi, int n_samples, int n_eta, float weight, float* rho0, int store_rho0,
@@ -162,13 +164,24 @@ int cplane_blocks_per_sm(int variant, int max_unit_slots);
 int zlines_reg_blocks_per_sm(int form);
 // variant 0: the row form (y lines, 36-row step, y lines); 1, 2: one cluster of 8 CTAs per plane
 // with 32 / 18 warps per CTA
-void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant);
-// form 0 / 1: register-ended Stockham tiles of 16 / 32 columns, 2: warp-FFT tiles of 16 columns
+// (line_form 3: the row form's y lines by the two-stage 16 x 18 transform; 4: its rows as well)
+void cplane_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int variant, int line_form = 0);
+// form 0 / 1: register-ended Stockham tiles of 16 / 32 columns, 2: warp-FFT tiles of 16 columns,
+// 3, 4: the two-stage 16 x 18 transform on tiles of 16 columns
 void zlines_reg(float2* W, int batch, int kind, int form, float kscale, float ecut, const float2* tw, cudaStream_t st);
 // the row form's passes one by one (the library times them separately): y lines in place on W
-// (dir +1 inverse, -1 forward) and the 36-row step
-void lines288(float2* W, int batch, int dir, const float2* tw, cudaStream_t st);
-void rows36_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st);
+// (dir +1 inverse, -1 forward; forms 3, 4 two-stage, else radix stages) and the 36-row step (form
+// 4: rows by the two-stage transform, else by warp FFTs)
+void lines288(float2* W, int batch, int dir, int form, const float2* tw, cudaStream_t st);
+void rows36_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st, int form = 0);
+// the two-stage 16 x 18 line transforms of the 288 grid (kernels_lines288.cu)
+cudaError_t lines288_2s_init_attributes();
+int lines288_2s_blocks_per_sm();
+void ylines288_2s(float2* W, int batch, int dir, const float2* tw, cudaStream_t st);
+void zlines288_2s(float2* W, int batch, int kind, float kscale, float ecut, const float2* tw, cudaStream_t st);
+cudaError_t rows36_2s_init_attributes(int max_unit_slots);
+int rows36_2s_blocks_per_sm(int max_unit_slots);
+void rows36_2s_step(const StepArgs& a, int batch, const float2* tw, cudaStream_t st);
 
 // ---- other kernels (kernels_misc.cu)
 void launch_noise(int ng, uint64_t seed, uint32_t stream_id, int sample0, int n_samples, int n_vec,

@@ -47,7 +47,7 @@ def test_tuning_is_only_a_hint():
         assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1]), setting
     chosen = c.autotune(8, reps=1)
     assert len(chosen) == c.TUNE_KEYS and chosen[0] in (0, 1) and chosen[3] in (0, 1, 2) and min(chosen) >= 0
-    assert chosen[4] == 0                    # the z-line form is tuned on the 288 grid only
+    assert chosen[4] == 0                    # the line form is tuned on the 288 grid only
     assert [c.get_tuning(k) for k in range(c.TUNE_KEYS)] == chosen
     got = _run(c, s)
     assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
@@ -57,7 +57,7 @@ def test_tuning_rejects_bad_keys_and_values():
     build.build()
     s = gc.small_cluster()
     c = _ctx(s, 4)
-    for key, val in ((5, 0), (-1, 0), (0, 2), (1, -5), (2, -1), (3, 3), (4, 3), (4, -1)):
+    for key, val in ((5, 0), (-1, 0), (0, 2), (1, -5), (2, -1), (3, 3), (4, 5), (4, -1)):
         with pytest.raises(RuntimeError):
             c.set_tuning(key, val)
     with pytest.raises(RuntimeError):
