@@ -71,8 +71,9 @@ TRAFFIC = {
     ('plane_step', 64): dict(ratio=839.2 / 806.4, source='kernels_grid.cu', sha='', capture='64-vector launch'),
     # k_rows36_step, third term of a 4-vector kernel_bench step: 5.815 GB read + written against
     # 4.998 GB algorithmic
-    ('plane_step', 288): dict(ratio=5.815 / 4.998, sha='864355dd4e601b8c', capture='4-vector launch',
-                              source=('kernels_cluster.cu', 'kb_unit.cuh', 'warp_fft.cuh')),
+    # under operand setting 3 (L2 prefetch + streaming caching) and a line form that keeps warp-FFT rows
+    ('plane_step', 288): dict(ratio=None, sha='', capture='4-vector launch', operands=(3,), line_forms=(0, 1, 2, 3),
+                              source=('kernels_cluster.cu', 'kb_unit.cuh', 'warp_fft.cuh', 'grid_common.cuh')),
 }
 
 
@@ -191,7 +192,7 @@ def units_per_step(cfg):
     return cfg['n'] ** 3 * 2 * cfg['n_eta'] * step_samples(cfg) * steps
 
 
-def roofline(prof, peaks, n):
+def roofline(prof, peaks, n, tuning=None):
     """Dominant kernel kind by device time; achieved = its algorithmic bytes / its event time."""
     kinds = {k: v for k, v in prof.items() if v['launches'] > 0 and v['alg_bytes'] > 0}
     total = sum(v['ms'] for v in prof.values())
@@ -201,6 +202,9 @@ def roofline(prof, peaks, n):
     peak = peaks['hbm_gbs']
     shares = {k: round(x['ms'] / total, 4) for k, x in prof.items() if x['launches']}
     tr = TRAFFIC.get((name, n))
+    ops, form = (tuning[0], tuning[4]) if tuning else (1, 0)
+    if tr is not None and (form not in tr.get('line_forms', (form,)) or ops not in tr.get('operands', (ops,))):
+        tr = None                        # another kernel or cache policy does this kind's work here
     traffic, tsrc = None, 'no ncu capture of the current kernel source'
     if tr is not None and tr['sha'] and tr['sha'] == source_sha(tr['source']):
         traffic = round(tr['ratio'] * v['alg_bytes'] / v['launches'])
@@ -434,7 +438,7 @@ def measure_large(args, cfg, local, world, rank, dist, peaks):
     h2d = noise_h.numel() * 8 + filt_h.numel() * 8 + phi_h.numel() * 4
     e2e = dict(value=replicas.job_throughput(units_per_step(cfg), args.steps, world, ms_e2e), unit=UNIT,
                h2d_bytes_per_step=int(h2d), d2h_bytes_per_step=int(sig_h.numel() * 16 + x_h.numel() * 8 + 32))
-    rl = roofline(prof, peaks, n)
+    rl = roofline(prof, peaks, n, pl.tuning)
     peak_gb = round(torch.cuda.max_memory_allocated(local) / 1e9, 1)
     pl.ctx.close()
     tuning = dict(zip(('plane_operand_prefetch', 'plane_lookahead', 'pencil_lookahead', 'plane_variant',

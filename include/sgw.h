@@ -91,10 +91,13 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
  * Launch tuning (the paper's GPU port batches all vectors of a step into each launch, Sec. 2.3;
  * these keys refine how those launches use the memory system).  Every key is a performance hint:
  * no result depends on it.
- *   SGW_TUNE_PLANE_OPERANDS   : 1 = each xy-plane pass block starts by prefetching into L2 the
- *                               operands of its pointwise step (b_{k+1}, psi, b_{k+2}, potential
- *                               rows), so they arrive while its inverse transform runs; 0 = off
- *                               (default 1)
+ *   SGW_TUNE_PLANE_OPERANDS   : bit 0 (1) = each xy-plane pass block starts by prefetching into L2
+ *                               the operands of its pointwise step (b_{k+1}, psi, b_{k+2},
+ *                               potential rows), so they arrive while its inverse transform runs;
+ *                               bit 1 (2, the 288 grid's 36-row step only) = b_{k+1}, psi, b_{k+2}
+ *                               are read and the step's outputs written with evict-first
+ *                               (streaming) caching, so that they do not displace prefetched or
+ *                               shared lines in L2; values 0-3 (default 1)
  *   SGW_TUNE_PLANE_LOOKAHEAD  : each xy-plane pass block also prefetches into L2 the input plane of
  *                               the block this many blocks later in launch order (0 = off, default)
  *   SGW_TUNE_PENCIL_LOOKAHEAD : the same for the z-pencil pass, in pencil blocks (0 = off, default)
@@ -118,7 +121,7 @@ sgw_status sgw_set_graph_mode(sgw_ctx* ctx, int enable);
  * On row-path grids (n = 48, 96, 288) the other keys are accepted and have no effect, and the
  * autotuner keeps their current values; SGW_TUNE_PLANE_VARIANT, SGW_TUNE_LINE_FORM and
  * SGW_TUNE_PLANE_OPERANDS (for the row form's 36-row step) act at n = 288.
- * sgw_set_tuning returns SGW_EINVAL for an unknown key or a negative value (a value above 1 for
+ * sgw_set_tuning returns SGW_EINVAL for an unknown key or a negative value (a value above 3 for
  * SGW_TUNE_PLANE_OPERANDS, above 2 for SGW_TUNE_PLANE_VARIANT, above 4 for SGW_TUNE_LINE_FORM) and drops the context's cached graphs; sgw_get_tuning writes the current
  * value to *value_host.
  */

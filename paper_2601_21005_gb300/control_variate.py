@@ -181,8 +181,11 @@ class ControlVariate:
         if F_cheap is None:
             self.pl.ctx.cv_rows(None, None, Y_paired, None, None, rows)
         else:
-            Yl = t.empty_like(Y_paired)          # Y - f_lin(x_paired) + mean f_lin(x_cheap)
-            self.pl.ctx.cv_linear_rows(self.lin, self._shells(F_cheap), self._shells(F_paired), Y_paired, Yl)
+            if self.linear:                      # Y - f_lin(x_paired) + mean f_lin(x_cheap)
+                Yl = t.empty_like(Y_paired)
+                self.pl.ctx.cv_linear_rows(self.lin, self._shells(F_cheap), self._shells(F_paired), Y_paired, Yl)
+            else:                                # no linear part: f_lin = 0 (its unfitted buffer holds no scales)
+                Yl = Y_paired
             if self.use_net:
                 self.pl.ctx.cv_rows(self._predict(F_cheap), self._predict(F_paired), Yl, self.mu, self.sd, rows)
             else:

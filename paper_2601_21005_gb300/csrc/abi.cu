@@ -762,7 +762,7 @@ static sgw_status split_factors(sgw_ctx* ctx, double dt, const float2** out) {
 sgw_status sgw_set_tuning(sgw_ctx* ctx, int key, int value) {
     if (!ctx) return fail(nullptr, SGW_EINVAL, "null context");
     if (key < 0 || key >= SGW_TUNE_KEYS) return fail(ctx, SGW_EINVAL, "unknown tuning key");
-    if (value < 0 || (key == SGW_TUNE_PLANE_OPERANDS && value > 1) || (key == SGW_TUNE_PLANE_VARIANT && value > 2) ||
+    if (value < 0 || (key == SGW_TUNE_PLANE_OPERANDS && value > 3) || (key == SGW_TUNE_PLANE_VARIANT && value > 2) ||
         (key == SGW_TUNE_LINE_FORM && value > 4))
         return fail(ctx, SGW_EINVAL, "tuning value out of range");
     clear_graphs(ctx);
@@ -835,7 +835,7 @@ sgw_status sgw_autotune(sgw_ctx* ctx, int batch, int reps, int* chosen_host) {
         if (key == SGW_TUNE_LINE_FORM) cand = sgw::cluster_plane(ctx->n) ? std::vector<int>{0, 1, 2, 3, 4}
                                                                           : std::vector<int>{ctx->tune[key]};
         else if (key == SGW_TUNE_PLANE_VARIANT && sgw::cluster_plane(ctx->n)) cand = {0, 1, 2};
-        else if (key == SGW_TUNE_PLANE_OPERANDS && sgw::cluster_plane(ctx->n)) cand = {0, 1};
+        else if (key == SGW_TUNE_PLANE_OPERANDS && sgw::cluster_plane(ctx->n)) cand = {0, 1, 2, 3};
         else if (sgw::rows_path(ctx->n)) cand = {ctx->tune[key]};   // the row kernels take no other launch hints
         int best_v = 0;
         float best = 1e30f;

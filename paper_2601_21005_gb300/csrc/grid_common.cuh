@@ -16,6 +16,13 @@ __device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
 __device__ __forceinline__ void st4(float2* p, float2 a, float2 b) {
     *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
 }
+// Streaming forms (data read or written once per launch): the lines are cached evict-first, so
+// they displace neither the operands prefetched into L2 for later blocks nor the data shared by
+// the vectors of one unit.
+__device__ __forceinline__ float4 ldcs4(const float2* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void stcs4(float2* p, float2 a, float2 b) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(a.x, a.y, b.x, b.y));
+}
 
 // Sum 8 per-lane values over a warp by halving exchanges at lane distances 16, 8, 4 (each lane keeps
 // the half selected by its lane bit and adds its partner's copy of that half), then a plain

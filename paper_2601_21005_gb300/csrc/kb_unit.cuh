@@ -84,8 +84,9 @@ __device__ __forceinline__ void kb_project_unit(const StepArgs& a, int u, int b,
 
 // The pointwise part of the fused step on ROWS x N unit points starting at global offset `off`
 // (vector b's unit; sm holds H_kin b1 + V_NL b1 at pitch P): out = cpsi psi + ch alpha (h + (V - Ebar) b1
-// [+ dv b1_partner]) + c2 b2, written to global memory and back into sm.
-template <int N, int ROWS, int P, int NT, int UNROLL = 2, int LAYOUT = 0>
+// [+ dv b1_partner]) + c2 b2, written to global memory and back into sm.  STREAM: b1, psi, b2 read and
+// out written with evict-first caching.
+template <int N, int ROWS, int P, int NT, int UNROLL = 2, int LAYOUT = 0, bool STREAM = false>
 __device__ __forceinline__ void step_pointwise(const StepArgs& a, const VecInfo& inf, size_t off, size_t uoff,
                                                float2* sm) {
     constexpr size_t NG = (size_t)N * N * N;
@@ -101,7 +102,7 @@ __device__ __forceinline__ void step_pointwise(const StepArgs& a, const VecInfo&
         // x is even: x + 1 sits one slot further (layout 0) or one group of 19 further (layout 1)
         const int sp = unit_pos_yx<N, P, LAYOUT>(y, x), sp1 = sp + (LAYOUT == 1 ? 19 : 1);
         float2 h0 = sm[sp], h1 = sm[sp1];
-        const float4 bb = ld4(a.b1 + off + o);
+        const float4 bb = STREAM ? ldcs4(a.b1 + off + o) : ld4(a.b1 + off + o);
         const float2 v = __ldg(reinterpret_cast<const float2*>(V + o));
         h0.x += (v.x - ebar) * bb.x;
         h0.y += (v.x - ebar) * bb.y;
@@ -109,7 +110,7 @@ __device__ __forceinline__ void step_pointwise(const StepArgs& a, const VecInfo&
         h1.y += (v.y - ebar) * bb.w;
         if (dV != nullptr) {
             const float2 d = __ldg(reinterpret_cast<const float2*>(dV + o));
-            const float4 pb = ld4(bp + o);
+            const float4 pb = ld4(bp + o);            // the partner's b1: another vector's launch reads it too
             h0.x += d.x * pb.x;
             h0.y += d.x * pb.y;
             h1.x += d.y * pb.z;
@@ -117,16 +118,19 @@ __device__ __forceinline__ void step_pointwise(const StepArgs& a, const VecInfo&
         }
         float2 o0 = cmul(ch, cscale(h0, alpha)), o1 = cmul(ch, cscale(h1, alpha));
         if (a.psi != nullptr) {
-            const float4 pp = ld4(a.psi + off + o);
+            const float4 pp = STREAM ? ldcs4(a.psi + off + o) : ld4(a.psi + off + o);
             o0 = cadd(o0, cmul(cpsi, make_float2(pp.x, pp.y)));
             o1 = cadd(o1, cmul(cpsi, make_float2(pp.z, pp.w)));
         }
         if (a.b2 != nullptr) {
-            const float4 b2 = ld4(a.b2 + off + o);
+            const float4 b2 = STREAM ? ldcs4(a.b2 + off + o) : ld4(a.b2 + off + o);
             o0 = cadd(o0, cmul(c2, make_float2(b2.x, b2.y)));
             o1 = cadd(o1, cmul(c2, make_float2(b2.z, b2.w)));
         }
-        st4(a.out + off + o, o0, o1);
+        if (STREAM)
+            stcs4(a.out + off + o, o0, o1);
+        else
+            st4(a.out + off + o, o0, o1);
         sm[sp] = o0;
         sm[sp1] = o1;
     }

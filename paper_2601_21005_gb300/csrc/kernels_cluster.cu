@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(ZT_NT, 4) k_ylines288(float2* __restrict__ W, 
 // unit's rows are copied into shared memory by 16-byte cp.async copies (all in flight at once, no
 // registers held), each row is transformed along x by a warp FFT in place, then the KB apply, the
 // pointwise step and the KB partials, then a warp transforms each row forward and the rows are
-// written out.  With a.pf_operands thread 0 first asks L2 for the unit's pointwise operands (b1, psi,
+// written out.  With bit 0 of a.pf_operands thread 0 first asks L2 for the unit's pointwise operands (b1, psi,
 // b2, potential rows) so that they arrive while the transforms run (a launch hint).
 constexpr int PR36 = CN + 2;            // row pitch of the 36-row step: rows start on 16-byte boundaries
 
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    if (a.pf_operands && threadIdx.x == 0) {
+    if ((a.pf_operands & 1) && threadIdx.x == 0) {
         l2_prefetch(a.b1 + off, UB);
         if (a.psi != nullptr) l2_prefetch(a.psi + off, UB);
         if (a.b2 != nullptr) l2_prefetch(a.b2 + off, UB);
@@ -284,7 +284,11 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
     }
     __syncthreads();
     if (kc != nullptr) kb_apply_unit<CN, PR36, CNT>(a, u, kcs, rowb);
-    step_pointwise<CN, CS, PR36, CNT, 4>(a, inf, off, uoff, rowb);
+    const bool stream = (a.pf_operands & 2) != 0;
+    if (stream)
+        step_pointwise<CN, CS, PR36, CNT, 4, 0, true>(a, inf, off, uoff, rowb);
+    else
+        step_pointwise<CN, CS, PR36, CNT, 4>(a, inf, off, uoff, rowb);
     if (a.Wout == nullptr) return;
     __syncthreads();
     if (a.kbp != nullptr) kb_project_unit<CN, PR36, CNT>(a, u, b, rowb);
@@ -304,7 +308,10 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_step(StepArgs a, const fl
 #pragma unroll 4
         for (int q = threadIdx.x; q < CS * CN / 2; q += CNT) {
             const int y = q / (CN / 2), x = 2 * (q % (CN / 2));
-            st4(dst + y * CN + x, rowb[y * PR36 + x], rowb[y * PR36 + x + 1]);
+            if (stream)
+                stcs4(dst + y * CN + x, rowb[y * PR36 + x], rowb[y * PR36 + x + 1]);
+            else
+                st4(dst + y * CN + x, rowb[y * PR36 + x], rowb[y * PR36 + x + 1]);
         }
     }
 }

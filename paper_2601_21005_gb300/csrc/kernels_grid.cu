@@ -442,7 +442,7 @@ k_plane_step(StepArgs a, const float2* __restrict__ tw) {
     constexpr int P = N + 1;
     const int z = blockIdx.x, b = blockIdx.y;
     // the pointwise operands stream into L2 while the inverse transform runs
-    if (threadIdx.x == 0 && a.pf_operands) prefetch_operands<N>(a, z, b);
+    if (threadIdx.x == 0 && (a.pf_operands & 1)) prefetch_operands<N>(a, z, b);
     if (threadIdx.x == 0 && a.pf_ahead > 0) {
         const long nxt = (long)b * N + z + a.pf_ahead;         // linear id of a later block
         if (nxt < (long)gridDim.y * N) l2_prefetch(a.W + (size_t)nxt * N * N, N * N * sizeof(float2));
@@ -487,7 +487,7 @@ k_plane_step_pipe(StepArgs a, const float2* __restrict__ tw, int total) {
     int t = blockIdx.x;
     if (t < total) {
         copy_plane_async<N, NT>(sm, a.W + (size_t)t * N * N);
-        if (threadIdx.x == 0 && a.pf_operands) prefetch_operands<N>(a, t % N, t / N);
+        if (threadIdx.x == 0 && (a.pf_operands & 1)) prefetch_operands<N>(a, t % N, t / N);
     }
     cp_async_commit();
     for (int it = 0; t < total; ++it, t += gridDim.x) {
@@ -495,7 +495,7 @@ k_plane_step_pipe(StepArgs a, const float2* __restrict__ tw, int total) {
         const int tn = t + gridDim.x;
         if (tn < total) {
             copy_plane_async<N, NT>(sm + (size_t)((it + 1) & 1) * N * P, a.W + (size_t)tn * N * N);
-            if (threadIdx.x == 0 && a.pf_operands) prefetch_operands<N>(a, tn % N, tn / N);
+            if (threadIdx.x == 0 && (a.pf_operands & 1)) prefetch_operands<N>(a, tn % N, tn / N);
         }
         cp_async_commit();
         cp_async_wait<1>();                 // this plane's group has landed (the newest may be in flight)

@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_2s(StepArgs a, const floa
     const size_t uoff = (size_t)u * R2S * R2N;
     const size_t off = (size_t)b * NG + uoff;
     const VecInfo inf = a.info[b];
-    if (a.pf_operands && threadIdx.x == 0) {
+    if ((a.pf_operands & 1) && threadIdx.x == 0) {
         l2_prefetch(a.b1 + off, UB);
         if (a.psi != nullptr) l2_prefetch(a.psi + off, UB);
         if (a.b2 != nullptr) l2_prefetch(a.b2 + off, UB);
@@ -174,7 +174,11 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_2s(StepArgs a, const floa
     }
     __syncthreads();
     if (kc != nullptr) kb_apply_unit<R2N, R2P, CNT, 1>(a, u, kcs, rowb);
-    step_pointwise<R2N, R2S, R2P, CNT, 4, 1>(a, inf, off, uoff, rowb);
+    const bool stream = (a.pf_operands & 2) != 0;
+    if (stream)
+        step_pointwise<R2N, R2S, R2P, CNT, 4, 1, true>(a, inf, off, uoff, rowb);
+    else
+        step_pointwise<R2N, R2S, R2P, CNT, 4, 1>(a, inf, off, uoff, rowb);
     if (a.Wout == nullptr) return;
     __syncthreads();
     if (a.kbp != nullptr) kb_project_unit<R2N, R2P, CNT, 1>(a, u, b, rowb);
@@ -199,8 +203,13 @@ __global__ void __launch_bounds__(NW * 32, 2) k_rows36_2s(StepArgs a, const floa
 #pragma unroll
             for (int m2 = 0; m2 < 16; ++m2) v[m2] = g[19 * m2];
             dft16<-1>(v);
+            if (stream) {
 #pragma unroll
-            for (int k2 = 0; k2 < 16; ++k2) dst[r * R2N + k1 + 18 * k2] = v[k2];
+                for (int k2 = 0; k2 < 16; ++k2) __stcs(dst + r * R2N + k1 + 18 * k2, v[k2]);
+            } else {
+#pragma unroll
+                for (int k2 = 0; k2 < 16; ++k2) dst[r * R2N + k1 + 18 * k2] = v[k2];
+            }
         }
     }
 }

@@ -112,6 +112,15 @@ def test_cluster_launch_choices_and_batches_are_bit_identical(large288):
         # sums differently from the radix stages: equal to FP32 rounding
         assert gc.rel_err(xd.cpu().numpy(), ref.cpu().numpy()) < 1e-5, (variant, form)
     c.set_tuning(c.TUNE_PLANE_VARIANT, 0)
+    # the operand hints (L2 prefetch, streaming cache policy) change no arithmetic: the same bits
+    for form in (0, 4):
+        c.set_tuning(c.TUNE_LINE_FORM, form)
+        for ops in (0, 2, 3):
+            c.set_tuning(c.TUNE_PLANE_OPERANDS, ops)
+            xd = gc.to_dev(x.reshape(3, -1), torch, torch.complex64)
+            c.propagate(xd, 1, 0.05, 8)
+            assert torch.equal(xd, outs[(0, form)]), (form, ops)
+    c.set_tuning(c.TUNE_PLANE_OPERANDS, 1)
     c.set_tuning(c.TUNE_LINE_FORM, 0)
     one = gc.to_dev(x[1].reshape(1, -1), torch, torch.complex64)
     c.propagate(one, 1, 0.05, 8)

@@ -57,7 +57,7 @@ def test_tuning_rejects_bad_keys_and_values():
     build.build()
     s = gc.small_cluster()
     c = _ctx(s, 4)
-    for key, val in ((5, 0), (-1, 0), (0, 2), (1, -5), (2, -1), (3, 3), (4, 5), (4, -1)):
+    for key, val in ((5, 0), (-1, 0), (0, 4), (1, -5), (2, -1), (3, 3), (4, 5), (4, -1)):
         with pytest.raises(RuntimeError):
             c.set_tuning(key, val)
     with pytest.raises(RuntimeError):
