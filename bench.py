@@ -71,8 +71,11 @@ TRAFFIC = {
     ('plane_step', 64): dict(ratio=839.2 / 806.4, source='kernels_grid.cu', sha='', capture='64-vector launch'),
     # k_rows36_step, third term of a 4-vector kernel_bench step: 5.815 GB read + written against
     # 4.998 GB algorithmic
-    # under operand setting 3 (L2 prefetch + streaming caching) and a line form that keeps warp-FFT rows
-    ('plane_step', 288): dict(ratio=None, sha='', capture='4-vector launch', operands=(3,), line_forms=(0, 1, 2, 3),
+    # k_rows36_step under operand setting 3 (L2 prefetch + streaming caching) and a line form that keeps
+    # warp-FFT rows; third term of a 4-vector kernel_bench step: 3.693 GB read + 1.487 GB written
+    # against 4.998 GB algorithmic
+    ('plane_step', 288): dict(ratio=(3.693 + 1.487) / 4.998, sha='08708691caeb2555', capture='4-vector launch',
+                              operands=(3,), line_forms=(0, 1, 2, 3),
                               source=('kernels_cluster.cu', 'kb_unit.cuh', 'warp_fft.cuh', 'grid_common.cuh')),
 }
 
