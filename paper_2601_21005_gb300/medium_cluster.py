@@ -35,6 +35,7 @@ def main():
     ap.add_argument('--paired-batches', type=int, default=4, help='runs of 16 paired samples')
     ap.add_argument('--cheap', type=int, default=4096)
     ap.add_argument('--ks-degree', type=int, default=4000)
+    ap.add_argument('--ks-iter', type=int, default=30, help='interior-solver iterations')
     args = ap.parse_args()
     build.build()
     n, h = 128, 0.5
@@ -44,7 +45,7 @@ def main():
     kctx.set_potential(torch.as_tensor(s['vloc'].reshape(-1).astype(np.float32)).cuda(), s['kb_atoms'])
     (emin, emax), _ = kctx.spectral_bounds(200, 1000, 0.05)
     e_homo, e_lumo, phi, info = states_near_gap(kctx, s['n_occ'], emin, emax, m=16, count_degree=3000,
-                                                window_degree=args.ks_degree, max_iter=30)
+                                                window_degree=args.ks_degree, max_iter=args.ks_iter)
     kctx.close()
     ks = dict(e_homo=e_homo, e_lumo=e_lumo, gap_eV=(e_lumo - e_homo) * HA_EV, max_residual=info['max_residual'],
               gap_centre=info['gap_centre'], seconds=round(time.perf_counter() - t0, 1))
