@@ -42,6 +42,7 @@ class ControlVariate:
         self.max_batch = max_batch
         self.ridge = ridge
         self.linear = linear        # False: no linear part (f_lin = 0), the network alone on Y
+        self.linear_used = linear   # False when the fitted linear part failed its hold-out test
         self.lin = torch.zeros(_sgw.sgw_cv_linear_size(self.n_feat, self.n_out), dtype=torch.float64,
                                device=pipeline.dev)
         self.use_net = True
@@ -105,20 +106,32 @@ class ControlVariate:
         return out
 
     # -------------------------------------------------------------- network
-    def train(self, F, Y, epochs=300, batch=64, lr=1e-3, holdout=0.2):
+    def train(self, F, Y, epochs=300, batch=64, lr=1e-3, holdout=0.2, eps_ks=None):
         with self.pl.on_stream():
-            return self._train(F, Y, epochs, batch, lr, holdout)
+            return self._train(F, Y, epochs, batch, lr, holdout, eps_ks)
 
-    def _train(self, F, Y, epochs, batch, lr, holdout):
+    def _train(self, F, Y, epochs, batch, lr, holdout, eps_ks=None):
         """Fit the linear part, then the network on its residuals; the network parameters of the
-        epoch with the lowest held-out loss are kept.  Returns (training losses, held-out losses)."""
+        epoch with the lowest held-out loss are kept.  With eps_ks (the target's KS energy) the
+        linear part is held out too: the QP standard error of the held-out samples' rows with it
+        (the training samples standing in for the cheap set) must be 2% below that of their plain
+        rows, else it is dropped (f_lin = 0).  Returns (training losses, held-out losses)."""
         t, ctx = self.torch, self.pl.ctx
         n = F.shape[0]
         nv = max(1, int(round(holdout * n))) if n > 4 else 0
         ntr = n - nv
+        self.linear_used = self.linear
         if self.linear:
             Fs = self._shells(F)
             ctx.cv_linear_fit(Fs[:ntr].contiguous(), Y[:ntr].contiguous(), self.ridge, self.lin)
+            if eps_ks is not None and nv >= 4:
+                Yv = Y[ntr:].clone()                 # fresh (aligned) buffers for the row slices
+                rows = t.empty_like(Yv)
+                ctx.cv_linear_rows(self.lin, Fs[:ntr].clone(), Fs[ntr:].clone(), Yv, rows)
+                se_lin = self.pl.qp(*self.plain_rows(rows), eps_ks)['se']
+                se_plain = self.pl.qp(*self.plain_rows(Yv), eps_ks)['se']
+                self.linear_used = bool(se_lin < 0.98 * se_plain)
+        if self.linear_used:
             R = t.empty_like(Y)
             ctx.cv_linear_apply(self.lin, Fs, self.n_out, R, y=Y)     # residuals Y - f_lin(x)
             Y = R
@@ -181,10 +194,10 @@ class ControlVariate:
         if F_cheap is None:
             self.pl.ctx.cv_rows(None, None, Y_paired, None, None, rows)
         else:
-            if self.linear:                      # Y - f_lin(x_paired) + mean f_lin(x_cheap)
+            if self.linear_used:                 # Y - f_lin(x_paired) + mean f_lin(x_cheap)
                 Yl = t.empty_like(Y_paired)
                 self.pl.ctx.cv_linear_rows(self.lin, self._shells(F_cheap), self._shells(F_paired), Y_paired, Yl)
-            else:                                # no linear part: f_lin = 0 (its unfitted buffer holds no scales)
+            else:                                # no linear part: f_lin = 0 (an unfitted buffer holds no scales)
                 Yl = Y_paired
             if self.use_net:
                 self.pl.ctx.cv_rows(self._predict(F_cheap), self._predict(F_paired), Yl, self.mu, self.sd, rows)
@@ -230,7 +243,7 @@ def study(pl, eps_ks, n_train, paired_batches, n_cheap, sample0, plain_sample_s,
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     Yt, Ft = cv.collect(n_train, sample0 + 300000)
-    tr, va = cv.train(Ft, Yt, epochs=epochs, batch=64, lr=1e-3)
+    tr, va = cv.train(Ft, Yt, epochs=epochs, batch=64, lr=1e-3, eps_ks=eps_ks)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     st = torch.cuda.current_stream()
@@ -301,6 +314,7 @@ def study(pl, eps_ks, n_train, paired_batches, n_cheap, sample0, plain_sample_s,
                 se_eV_cv_rows=round(r_cv['se'] * HA_EV, 5), se_eV_cv_cheap_mean=round(r_cheap['se'] * HA_EV, 5),
                 variance_gain=round((r_pl['se'] / se_cv) ** 2, 3),
                 variance_gain_linear_part_alone=round((r_pl['se'] / se_lin) ** 2, 3), network_kept=bool(net_kept),
+                linear_part_kept=bool(cv.linear_used),
                 variance_gain_linear_plus_network=round((r_pl['se'] / se_both) ** 2, 3),
                 variance_gain_network_alone=round((r_pl['se'] / se_net) ** 2, 3),
                 network_alone_passed_holdout=bool(net_alone_kept), network_alone_train_seconds=round(t_net_alone, 2),

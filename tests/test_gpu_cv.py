@@ -254,8 +254,9 @@ def test_control_variate_gain_tiny():
                   cheb_deg=16, n_cheb=128, samples_per_batch=8, seed=3000, stream_id=1)
     cv = ControlVariate(pl, m2max=10, width=256, max_batch=256, seed=5)
     Yt, Ft = cv.collect(1024, 0)
-    tr, va = cv.train(Ft, Yt, epochs=200, batch=64, lr=1e-3)
+    tr, va = cv.train(Ft, Yt, epochs=200, batch=64, lr=1e-3, eps_ks=w[3])
     assert min(va) < va[0]
+    assert cv.linear_used                    # the linear part passes its hold-out test here
     Yp, Fp = cv.collect(256, 100000)
     Fc = cv.cheap_features(8192, 200000)
     S0, X0 = cv.plain_rows(Yp)
