@@ -139,8 +139,9 @@ sgw_status sgw_get_tuning(sgw_ctx* ctx, int key, int* value_host);
 /*
  * Autotuner: time `reps` degree-8 Chebyshev sums (the propagator's two-pass term, KB included when
  * a KB part is set) on a scratch batch of `batch` vectors for each candidate value (plane-pass
- * variant 0/1/2, then operand prefetch 0/1, then the lookaheads 0 and 1/2, 1, 3/2, 2 waves of resident
- * blocks from the occupancy of this GPU, then the line form 0-4 at n = 288), keep the fastest per key, each key timed with the
+ * variant 0/1/2, then the operand hints 0/1 (0-3 at n = 288), then the lookaheads 0 and 1/2, 1, 3/2,
+ * 2 waves of resident blocks from the occupancy of this GPU, then the line form 0-4 at n = 288), keep
+ * the fastest per key, each key timed with the
  * choices already made for the keys before it, and write the chosen values to chosen_host
  * [SGW_TUNE_KEYS] (may be NULL).  Needs sgw_set_potential and a spectral interval (SGW_ESTATE
  * otherwise); 1 <= batch <= max_batch and reps >= 1 (SGW_EINVAL otherwise).  Uses a context work
