@@ -128,9 +128,12 @@ class ControlVariate:
                 Yv = Y[ntr:].clone()                 # fresh (aligned) buffers for the row slices
                 rows = t.empty_like(Yv)
                 ctx.cv_linear_rows(self.lin, Fs[:ntr].clone(), Fs[ntr:].clone(), Yv, rows)
-                se_lin = self.pl.qp(*self.plain_rows(rows), eps_ks)['se']
-                se_plain = self.pl.qp(*self.plain_rows(Yv), eps_ks)['se']
-                self.linear_used = bool(se_lin < 0.98 * se_plain)
+                try:
+                    se_lin = self.pl.qp(*self.plain_rows(rows), eps_ks)['se']
+                    se_plain = self.pl.qp(*self.plain_rows(Yv), eps_ks)['se']
+                    self.linear_used = bool(se_lin < 0.98 * se_plain)
+                except RuntimeError:
+                    pass                         # no QP root for the held-out rows: no verdict, keep it
         if self.linear_used:
             R = t.empty_like(Y)
             ctx.cv_linear_apply(self.lin, Fs, self.n_out, R, y=Y)     # residuals Y - f_lin(x)
