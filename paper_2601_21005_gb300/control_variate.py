@@ -132,8 +132,9 @@ class ControlVariate:
                     se_lin = self.pl.qp(*self.plain_rows(rows), eps_ks)['se']
                     se_plain = self.pl.qp(*self.plain_rows(Yv), eps_ks)['se']
                     self.linear_used = bool(se_lin < 0.98 * se_plain)
-                except RuntimeError:
-                    pass                         # no QP root for the held-out rows: no verdict, keep it
+                except _sgw.SgwError as e:
+                    if e.status != 6:            # SGW_ENOCONV: no QP root for the held-out rows
+                        raise                    # (no verdict: the linear part stays); anything else is an error
         if self.linear_used:
             R = t.empty_like(Y)
             ctx.cv_linear_apply(self.lin, Fs, self.n_out, R, y=Y)     # residuals Y - f_lin(x)
